@@ -1,0 +1,239 @@
+"""Pins for the oracle's Parallel-l0 (Alg. 2) and Serial-l0 (Alg. 1).
+
+The theorem-regime cases use the point-line incidence matrix of the affine
+plane AG(2, q) (q prime): its q^2 + q lines are the columns, its q^2 points
+the rows, d = q, and two columns share at most one row.  For those graphs the
+expansion parameter eps of Def. 2 is found by brute force over all column
+sets of size <= k, and Theorem 1 (with Lemmas 3-5 and Eq. (37)) then fixes
+what the decoder must do: accept only exact values x_j at the right j,
+shrink the support of x - x_hat by the factor of Eq. (37) every iteration,
+and end with x_hat = x, which brute force over all supports of size <= k
+confirms to be the unique sparsest solution.
+"""
+import itertools
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_1508_01256_gb300 import inputs
+
+
+def affine_plane(q):
+    lines = []
+    for s in range(q):
+        for c in range(q):
+            lines.append(sorted(a * q + (s * a + c) % q for a in range(q)))
+    for c in range(q):
+        lines.append(sorted(c * q + b for b in range(q)))
+    return np.array(lines, dtype=np.int32)
+
+
+def eps_star(A, m, k):
+    """max over 1 <= |S| <= k of 1 - |N(S)|/(d|S|): the graph is a
+    (k, eps, d)-expander exactly for eps > eps_star (Def. 2)."""
+    n, d = A.shape
+    nbrs = [frozenset(map(int, r)) for r in A]
+    worst = Fraction(0)
+    for size in range(1, k + 1):
+        for S in itertools.combinations(range(n), size):
+            u = frozenset().union(*(nbrs[j] for j in S))
+            worst = max(worst, 1 - Fraction(len(u), d * size))
+    return worst
+
+
+def dissociated(vals):
+    ints = [int(v) for v in np.rint(np.asarray(vals) * 2.0 ** 32)]
+    sums = set()
+    for size in range(len(ints) + 1):
+        for T in itertools.combinations(ints, size):
+            sums.add(sum(T))
+    return len(sums) == 2 ** len(ints)
+
+
+def dense(A, m):
+    n, _ = A.shape
+    M = np.zeros((m, n))
+    for j in range(n):
+        M[A[j], j] = 1.0
+    return M
+
+
+def unique_sparsest(M, y, k):
+    """All supports of size <= k whose least-squares fit reproduces y."""
+    m, n = M.shape
+    fits = []
+    for size in range(0, k + 1):
+        combos = np.array(list(itertools.combinations(range(n), size)), dtype=np.int64)
+        if size == 0:
+            if np.all(y == 0):
+                fits.append(())
+            continue
+        for chunk in np.array_split(combos, max(1, len(combos) // 4000)):
+            As = M[:, chunk].transpose(1, 0, 2)          # (N, m, size)
+            c = np.linalg.pinv(As) @ y                   # (N, size)
+            res = np.linalg.norm(As @ c[:, :, None] - y[None, :, None], axis=(1, 2))
+            for t in np.nonzero(res < 1e-9)[0]:
+                fits.append(tuple(chunk[t]))
+    return fits
+
+
+def _theorem_cases():
+    cases = []
+    for q, k in ((5, 3), (7, 3), (7, 4)):
+        for seed in range(3):
+            cases.append((q, k, seed))
+    return cases
+
+
+@pytest.mark.parametrize("q,k,seed", _theorem_cases())
+def test_theorem_regime(orc, q, k, seed):
+    rng = np.random.default_rng(1000 * q + 10 * k + seed)
+    A = affine_plane(q)
+    # random relabelling of rows keeps the incidence structure
+    perm = rng.permutation(q * q).astype(np.int32)
+    A = np.sort(perm[A], axis=1).astype(np.int32)
+    n, d = A.shape
+    m = q * q
+    es = eps_star(A, m, k)
+    assert es < Fraction(1, 4)
+    alpha = math.ceil((1 - 2 * es) * d)  # integer threshold of (1-2eps)d, eps -> eps*+
+    eps = float(es) + 1e-9
+    ratio = 2 * eps * d / (1 + math.floor(2 * eps * d))
+    ell_star = 0
+    while k * ratio ** ell_star >= 1:
+        ell_star += 1
+
+    x = np.zeros(n)
+    supp = np.sort(rng.choice(n, size=k, replace=False))
+    x[supp] = inputs.values(k, seed + 17 * q + k, "gauss-grid")
+    assert dissociated(x[supp])
+    y = orc.measure(A, m, x)
+
+    res = orc.parallel_l0(A, m, y, alpha=alpha, max_iter=50, trace=True)
+    assert res["status"] == orc.CONVERGED
+    assert np.array_equal(res["x_hat"], x)
+    assert res["iterations"] <= ell_star
+    h = res["r0_hist"]
+    assert np.all(np.diff(h) < 0)  # strict contraction of ||r||_0
+    # replay the trace: every accepted pair is (j, x_j) with j still wrong
+    xh = np.zeros(n)
+    for it, idx, om in res["trace"]:
+        S = set(np.nonzero(x - xh)[0])
+        assert len(idx) > 0
+        for j, w in zip(idx, om):
+            assert j in S and xh[j] == 0.0 and w == x[j]
+        xh[idx] += om
+        S_next = set(np.nonzero(x - xh)[0])
+        assert len(S_next) <= ratio * len(S) + 1e-12
+    # brute force: x is the only support of size <= k that explains y
+    fits = unique_sparsest(dense(A, m), y, k)
+    assert fits == [tuple(supp)]
+    # Serial-l0 (Alg. 1) also recovers x
+    ser = orc.serial_l0(A, m, y, alpha=alpha, max_iter=50)
+    assert ser["status"] == orc.CONVERGED and np.array_equal(ser["x_hat"], x)
+    assert ser["iterations"] <= res["iterations"]
+
+
+def test_k0_converges_immediately(orc):
+    A = orc.make_expander(300, 40, 5, 1)
+    res = orc.parallel_l0(A, 40, np.zeros(40))
+    assert res["status"] == orc.CONVERGED and res["iterations"] == 0
+    assert np.all(res["x_hat"] == 0) and list(res["r0_hist"]) == [0]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_k1_first_iteration_predicted(orc, seed):
+    """k = 1: all d rows of the support column j0 hold x_j0 (score d); any
+    other column with overlap o sees x_j0 o times and zero d - o times, so its
+    l0 decrease is 2o - d.  The first accepted set is therefore exactly
+    {j0} and the columns with 2o - d >= alpha; when that set is {j0} the
+    decode ends after one iteration with x_hat = x."""
+    n, m, d = 500, 60, 7
+    A = orc.make_expander(n, m, d, 40 + seed)
+    j0 = seed * 37 % n
+    ov = np.array([len(set(A[j]) & set(A[j0])) for j in range(n)])
+    predicted = sorted(set([j0]) | set(np.nonzero(2 * ov - d >= 2)[0].tolist()))
+    x = np.zeros(n)
+    x[j0] = inputs.values(1, seed, "gauss-grid")[0]
+    y = orc.measure(A, m, x)
+    res = orc.parallel_l0(A, m, y, trace=True)
+    it0, idx, om = res["trace"][0]
+    assert list(idx) == predicted and np.all(om == x[j0])
+    if predicted == [j0]:
+        assert res["status"] == orc.CONVERGED and res["iterations"] == 1
+        assert np.array_equal(res["x_hat"], x)
+
+
+def test_disjoint_neighbourhoods_one_iteration(orc):
+    n, m, d = 40, 120, 3
+    A = np.array([[3 * j + t for t in range(d)] for j in range(n)], dtype=np.int32)
+    supp = [0, 1, 2, 3, 4]  # all neighbourhoods pairwise disjoint
+    x = np.zeros(n)
+    x[supp] = inputs.values(5, 3, "gauss-grid")
+    y = orc.measure(A, m, x)
+    res = orc.parallel_l0(A, m, y)
+    assert res["status"] == orc.CONVERGED and res["iterations"] == 1
+    assert np.array_equal(res["x_hat"], x)
+
+
+def test_count_mode_spurious_acceptance(orc):
+    """Column 1 shares two rows with the support column 0 and sees one zero:
+    l0 decrease 2 - 1 = 1 < alpha, match count 2 >= alpha.  The two score
+    readings of Eq. (15) vs Alg. 8 part here."""
+    A = np.array([[0, 1, 2], [0, 1, 3], [2, 3, 4]], dtype=np.int32)
+    y = np.array([0.5, 0.5, 0.5, 0.0, 0.0])
+    l0 = orc.parallel_l0(A, 5, y, alpha=2)
+    assert l0["status"] == orc.CONVERGED and l0["iterations"] == 1
+    assert np.array_equal(l0["x_hat"], [0.5, 0.0, 0.0])
+    cnt = orc.parallel_l0(A, 5, y, alpha=2, score_mode=orc.SCORE_COUNT,
+                          max_iter=10, trace=True)
+    assert list(cnt["trace"][0][1]) == [0, 1]
+    assert cnt["status"] == orc.MAX_ITER  # it oscillates between two states
+
+
+def test_stalled_when_nothing_qualifies(orc):
+    A = np.array([[0, 1, 2], [2, 3, 4]], dtype=np.int32)
+    y = np.array([1.0, 2.0, 3.0, 4.0, 5.0])  # all distinct, not in range of A
+    res = orc.parallel_l0(A, 5, y)
+    assert res["status"] == orc.STALLED and res["iterations"] == 0
+    assert np.array_equal(res["r"], y)
+
+
+def test_max_iter_zero(orc):
+    A = np.array([[0, 1, 2]], dtype=np.int32)
+    res = orc.parallel_l0(A, 3, np.array([1.0, 1.0, 1.0]), max_iter=0)
+    assert res["status"] == orc.MAX_ITER and res["iterations"] == 0
+
+
+@pytest.mark.parametrize("model", ["gauss-grid", "gauss-raw", "pm1"])
+def test_convergence_invariant(orc, model):
+    """CONVERGED <=> r == 0 <=> y == A x_hat under the row-sum rule; the
+    returned r always equals y - A x_hat and r0 its l0 norm."""
+    for s in range(5):
+        p = inputs.make_problem(4096, 410, 7, 41 + 10 * s, 500 + s, model)
+        A = orc.make_expander(p.n, p.m, p.d, p.a_seed)
+        y = orc.measure(A, p.m, p.x)
+        res = orc.parallel_l0(A, p.m, y)
+        r_ref = y - dense(A, p.m) @ res["x_hat"] if model == "gauss-grid" else \
+            orc.residual(A, p.m, y, res["x_hat"])
+        assert np.array_equal(res["r"], r_ref)
+        assert res["r0_final"] == np.count_nonzero(res["r"]) == res["r0_hist"][-1]
+        conv = res["status"] == orc.CONVERGED
+        assert conv == (res["r0_final"] == 0)
+        if conv:
+            assert np.array_equal(orc.measure(A, p.m, res["x_hat"]), y)
+
+
+def test_small_workload_recovers(orc):
+    """n=4096, m=410, k=41, d=7 (rho = 0.1, well under the phase transition
+    of Sec. 5.1): every seeded instance is recovered exactly, in few
+    iterations (Sec. 5.4 reports O(log k) iterations)."""
+    for s in range(10):
+        p = inputs.plain_small(seed=s)
+        A = orc.make_expander(p.n, p.m, p.d, p.a_seed)
+        y = orc.measure(A, p.m, p.x)
+        res = orc.parallel_l0(A, p.m, y)
+        assert res["status"] == orc.CONVERGED and np.array_equal(res["x_hat"], p.x)
+        assert res["iterations"] <= math.ceil(math.log(41)) + 1
