@@ -1,0 +1,431 @@
+#!/usr/bin/env python
+"""Benchmark: Parallel-l0 decodes per second on one GB300 (or N, as replicas).
+
+One step = one complete Parallel-l0 decode (Alg. 2: score all columns, apply,
+recompute r and ||r||_0, until the stop rule) of a fresh instance of the
+workload, inputs resident in HBM.  Default workload: n=2^20, m=2^17,
+k=round(0.2 m)=26214, d=7, N(0,1) nonzeros on the 2^-32 grid, uniform
+support and expander, one instance per call.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank decodes its
+own instances (no data exchange) and the value is all ranks' decodes over the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Parallel-l0 decodes/s + HBM GB/s vs peak, batched vs plain; p99 latency"
+FALLBACK_HBM_GBS = 6800.0
+TABLE3_SECONDS = {22: 0.0167, 24: 0.0557, 26: 0.2319}  # Table 3, K40, rho=0.05, d=7
+
+
+def workload(name: str, seed: int):
+    from paper_1508_01256_gb300 import inputs
+    if name == "at-scale":
+        return inputs.plain_at_scale(seed=seed)
+    if name == "small":
+        return inputs.plain_small(seed=seed)
+    if name == "extreme":
+        return inputs.extreme_undersampling(0.05, d=9, seed=seed)
+    if name == "table3":
+        return inputs.extreme_undersampling(0.05, d=7, seed=seed)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(name: str, p) -> dict:
+    return {"workload": {"at-scale": "plain Parallel-l0 at scale",
+                         "small": "plain Parallel-l0, single small instance",
+                         "extreme": "extreme undersampling n/m ~ 10^3",
+                         "table3": "Table 3 shape (delta=1e-3, rho=0.05, d=7)"}[name],
+            "n": p.n, "m": p.m, "k": p.k, "d": p.d, "alpha": 2, "values": p.model,
+            "instances_per_step": 1}
+
+
+def vs_baseline(name: str, p, value: float):
+    if name == "table3" and p.n in (2 ** 22, 2 ** 24, 2 ** 26):
+        return value / (1.0 / TABLE3_SECONDS[p.n.bit_length() - 1])
+    return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        for key in ("hbm_gbs", "hbm_GBps", "hbm"):
+            if key in d:
+                return float(d[key]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def traffic_record(kernel: str, workload_name: str):
+    """Per-launch DRAM bytes from a committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    entry = rec.get(kernel, {}).get(workload_name)
+    if not entry:
+        return None
+    src = os.path.join(ROOT, "paper_1508_01256_gb300", "csrc", entry["source"])
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return entry["bytes_per_launch"] if sha == entry.get("source_sha") else None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.tmp is None:
+            return None
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (baseline / reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_instances(name: str, count: int, base_seed: int):
+    import oracle
+    insts = []
+    for i in range(count):
+        p = workload(name, base_seed + i)
+        A = oracle.make_expander(p.n, p.m, p.d, p.a_seed)
+        y = oracle.measure(A, p.m, p.x)
+        insts.append((p, A, y))
+    return insts
+
+
+def oracle_round(insts):
+    """Decode every instance concurrently, one host thread each (the oracle
+    itself is single-threaded); returns (wall seconds, all exact)."""
+    import numpy as np
+
+    import oracle
+    ok = [False] * len(insts)
+
+    def run(i):
+        p, A, y = insts[i]
+        res = oracle.parallel_l0(A, p.m, y)
+        ok[i] = res["status"] == oracle.CONVERGED and np.array_equal(res["x_hat"], p.x)
+
+    threads = [threading.Thread(target=run, args=(i,)) for i in range(len(insts))]
+    t0 = time.perf_counter()
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    return time.perf_counter() - t0, all(ok)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(name: str, budget_s: float = 12.0):
+    cores = host_cores()
+    insts = oracle_instances(name, cores, 777000)
+    decodes, elapsed, rounds, exact = 0, 0.0, 0, True
+    while elapsed < budget_s and rounds < 8:
+        dt, ok = oracle_round(insts)
+        elapsed += dt
+        decodes += len(insts)
+        rounds += 1
+        exact &= ok
+    return {"value": decodes / elapsed, "unit": "decodes/s", "cores": cores, "kind": "oracle",
+            "sample": f"{rounds} round(s) x {cores} concurrent single-threaded oracle decodes "
+                      f"of the same workload ({decodes} decodes, {elapsed:.1f} s)",
+            "exact_recovery": exact}
+
+
+def run_reference(args):
+    from paper_1508_01256_gb300 import inputs  # noqa: F401  (inputs only)
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = host_cores()
+    insts = oracle_instances(args.workload, cores, 555000)
+    for _ in range(args.warmup):
+        oracle_round(insts)
+    total, exact = 0.0, True
+    for _ in range(args.steps):
+        dt, ok = oracle_round(insts)
+        total += dt
+        exact &= ok
+    decodes = args.steps * len(insts)
+    value = decodes / total
+    p = insts[0][0]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "decodes/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": vs_baseline(args.workload, p, value),
+            "dtype": "f64", "data": "synthetic",
+            "config": dict(workload_config(args.workload, p), instances_per_step=cores),
+            "e2e": {"value": value, "unit": "decodes/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "cpu_baseline": {"value": value, "unit": "decodes/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"each step: {cores} concurrent single-threaded oracle "
+                                       f"decodes, one per host thread"},
+            "exact_recovery": exact, "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ccs(args):
+    import numpy as np
+    import torch
+
+    from paper_1508_01256_gb300 import build as libbuild
+    from paper_1508_01256_gb300 import ccs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    libbuild.build()
+    ccs.lib()
+
+    # instances resident in HBM
+    insts = []
+    for i in range(args.instances):
+        p = workload(args.workload, 1000 * rank + 17 + i)
+        csc, ptr, cols = ccs.make_expander(p.n, p.m, p.d, p.a_seed, device=dev)
+        y = ccs.measure(ptr, cols, torch.from_numpy(p.x).to(dev), p.m, p.d)
+        insts.append((p, csc, ptr, cols, y))
+    p0 = insts[0][0]
+    ws = ccs.workspace(ccs.ccs_workspace_size(ccs.OP_DECODE, p0.n, p0.m, p0.d), dev)
+    x_hat = torch.empty(p0.n, dtype=torch.float64, device=dev)
+    r = torch.empty(p0.m, dtype=torch.float64, device=dev)
+    hist = torch.full((101,), -1, dtype=torch.int64, device=dev)
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
+    stream = torch.cuda.current_stream(dev)
+
+    def decode(i):
+        p, csc, ptr, cols, y = insts[i % len(insts)]
+        return ccs.decode_parallel_l0(csc, ptr, cols, y, engine=args.engine, ws=ws,
+                                      out=(x_hat, r, hist))
+
+    for i in range(args.warmup):
+        flush.zero_()
+        decode(i)
+    torch.cuda.synchronize()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    iters = []
+    exact = True
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = ccs.ccs_launch_count()
+    ccs.ccs_profile_begin()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            out = decode(i)
+            evs[i][1].record(stream)
+            iters.append(out.iterations)
+            if out.status != ccs.CONVERGED:
+                exact = False
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    ktimes = ccs.ccs_profile_end()
+    launches = ccs.ccs_launch_count() - launches0
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_s = sum(step_ms) / 1000.0
+    # exactness of the last decode of each instance
+    for i in range(len(insts)):
+        o = decode(args.steps + i)
+        exact &= bool(np.array_equal(o.x_hat.cpu().numpy(), insts[(args.steps + i) % len(insts)][0].x))
+
+    # end to end through the public API: pinned host inputs -> device, decode,
+    # x_hat back to the host, every step
+    p, csc, ptr, cols, y = insts[0]
+    h_csc, h_ptr, h_cols, h_y = (t.cpu().pin_memory() for t in (csc, ptr, cols, y))
+    d_csc, d_ptr, d_cols, d_y = (torch.empty_like(t) for t in (csc, ptr, cols, y))
+    h_x = torch.empty(p.n, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in (h_csc, h_ptr, h_cols, h_y))
+    d2h = h_x.numel() * h_x.element_size()
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    e2e_t = 0.0
+    for i in range(e2e_steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for dst, src in ((d_csc, h_csc), (d_ptr, h_ptr), (d_cols, h_cols), (d_y, h_y)):
+            dst.copy_(src, non_blocking=True)
+        o = ccs.decode_parallel_l0(d_csc, d_ptr, d_cols, d_y, engine=args.engine, ws=ws,
+                                   out=(x_hat, r, hist))
+        h_x.copy_(o.x_hat, non_blocking=True)
+        torch.cuda.synchronize()
+        if i > 0:  # first pass is a warm-up
+            e2e_t += time.perf_counter() - t1
+
+    # max over ranks
+    decodes = args.steps
+    if dist is not None:
+        tt = torch.tensor([total_s, e2e_t], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_s, e2e_t = float(tt[0]), float(tt[1])
+    value = world * decodes / total_s
+    e2e_value = world * e2e_steps / e2e_t
+
+    # roofline of the dominant kernel (score): algorithmic bytes per launch =
+    # 4 d n (CSC row indices) + 8 m (one read of r)
+    sc_launches, sc_ms = ktimes.get("score", (0, 0.0))
+    res_launches, res_ms = ktimes.get("residual", (0, 0.0))
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if sc_launches:
+        bytes_per_launch = 4 * p0.d * p0.n + 8 * p0.m
+        avg_s = sc_ms / sc_launches / 1000.0
+        achieved = bytes_per_launch / avg_s / 1e9
+        roof = {"bound": "hbm", "kernel": "score", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                "traffic": traffic_record("score", args.workload),
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "avg_launch_us": avg_s * 1e6}
+    kernel_share = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in ktimes.items()}
+
+    if rank == 0:
+        cb = None
+        if world == 1 and not args.no_cpu_baseline:
+            cb = cpu_baseline(args.workload)
+        line = {"metric": METRIC, "value": value, "unit": "decodes/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1000.0 * total_s / decodes, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": vs_baseline(args.workload, p0, value),
+                "dtype": "f64", "data": "synthetic",
+                "config": dict(workload_config(args.workload, p0), engine=args.engine,
+                               l2="flushed between steps (512 MB write)",
+                               parallelism=f"replicas{world}"),
+                "e2e": {"value": e2e_value, "unit": "decodes/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches,
+                "roofline": roof,
+                "cpu_baseline": cb,
+                "clocks": clk.summary(),
+                "column_updates_per_s": value * p0.n * statistics.mean(iters),
+                "iterations_mean": statistics.mean(iters),
+                "exact_recovery": exact,
+                "kernel_times": kernel_share,
+                "wall_s_timed_region": wall}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ccs", choices=["ccs", "reference"])
+    ap.add_argument("--workload", default="at-scale",
+                    choices=["at-scale", "small", "extreme", "table3"])
+    ap.add_argument("--engine", type=int, default=0)
+    ap.add_argument("--instances", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ccs(args)
+
+
+if __name__ == "__main__":
+    main()

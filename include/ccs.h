@@ -1,0 +1,247 @@
+/*
+ * ccs.h -- C ABI of libccs, a GB300 (sm_103a) implementation of the
+ * Parallel-l0 expander decoder of Mendoza-Smith & Tanner, "Expander
+ * l0-decoding" (2015).
+ *
+ * Problem (Sec. 1): recover a k-sparse x in R^n from y = A x in R^m, where A
+ * is the 0/1 adjacency matrix of a left d-regular bipartite expander
+ * (Defs. 2-3, Sec. 2.2): column j has ones exactly in the d rows N(j).
+ *
+ * Conventions shared by every entry point:
+ *  - Array arguments are DEVICE pointers owned by the caller (for example
+ *    PyTorch tensors' data_ptr()).  The library never frees or keeps them.
+ *  - Scratch comes from a caller-owned device workspace of at least the size
+ *    the matching *_workspace_size() call reports; no call on the decode path
+ *    allocates device memory.  A workspace serves one call at a time.
+ *  - Work is issued on the caller's stream (a cudaStream_t; NULL is the
+ *    legacy default stream).  Calls that report a result to the host say
+ *    so and synchronise that stream before returning.
+ *  - Every call returns a status code (CCS_OK or a CCS_E* error); nothing
+ *    is thrown across the ABI.  ccs_last_error() describes the last failure
+ *    of the calling thread.  The decode outcome (converged / stalled /
+ *    iteration cap) is a field of ccs_result, not an error.
+ *  - Matrix layout: CSC row indices csc_rows[n*d], int32; column j's d
+ *    distinct rows sit at [j*d, (j+1)*d), ascending.  CSR (the transpose,
+ *    N(i) for every row i): csr_ptr[m+1] int64 offsets, csr_cols[n*d] int32,
+ *    columns ascending within each row.
+ *  - Values are IEEE binary64.  Every sum over a row runs in ascending
+ *    column order from +0.0, skipping zero entries; -0.0 counts as zero.
+ *    Inputs must be finite.
+ *  - Limits: 1 <= d <= 16, d <= m, n*d < 2^31.
+ */
+#ifndef CCS_H
+#define CCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define CCS_API __attribute__((visibility("default")))
+#else
+#define CCS_API
+#endif
+
+/* Same object as cudaStream_t, declared here so that this header does not
+ * need the CUDA headers. */
+typedef struct CUstream_st *ccs_stream_t;
+
+/* ---- status codes ------------------------------------------------------ */
+enum {
+    CCS_OK = 0,
+    CCS_EINVAL = 1,    /* bad argument or size outside the limits above      */
+    CCS_ENOMEM = 2,    /* workspace smaller than *_workspace_size()          */
+    CCS_ECUDA = 3,     /* a CUDA runtime call failed                         */
+    CCS_ETIMEOUT = 4,  /* a bounded device wait ran out (watchdog)           */
+    CCS_EBUDGET = 5,   /* serving: request does not fit the memory budget    */
+    CCS_EBUSY = 6      /* serving: no free slot / ticket not finished        */
+};
+
+/* ---- decode outcome (ccs_result.status) -------------------------------- */
+enum {
+    CCS_CONVERGED = 0, /* ||r||_0 == 0, i.e. y == A x_hat                     */
+    CCS_STALLED = 1,   /* an iteration accepted no pair: a fixed point       */
+    CCS_MAX_ITER = 2   /* params.max_iter iterations done                    */
+};
+
+/* ---- score (selection rule) -------------------------------------------- */
+enum {
+    /* Eq. (15): the l0 decrease ||r||_0 - ||r - omega a_j||_0, which for a
+     * 0/1 column with distinct rows equals c_omega - c_0 (matches of omega
+     * minus zeros among r_N(j)).  Default. */
+    CCS_SCORE_L0_DECREASE = 0,
+    /* Alg. 8 (and the rule of ER / LDDSR, Sec. 3): the match count c_omega. */
+    CCS_SCORE_COUNT = 1
+};
+
+/* ---- engines ------------------------------------------------------------ */
+enum {
+    CCS_ENGINE_AUTO = 0,       /* library's choice                           */
+    CCS_ENGINE_HOST_LOOP = 1,  /* one launch per phase, host checks the stop
+                                  rule after every iteration                 */
+    CCS_ENGINE_GRAPH = 2,      /* iteration loop in a CUDA graph with a
+                                  device-side conditional WHILE node         */
+    CCS_ENGINE_PERSISTENT = 3  /* one cooperative launch runs every
+                                  iteration; grid barriers between phases    */
+};
+
+typedef struct {
+    int32_t alpha;        /* accept when score >= alpha; 2 <= alpha <= d.
+                             The paper's real alpha in (1, d] is ceil(alpha).
+                             Default 2 (Sec. 5).                              */
+    int32_t max_iter;     /* iteration cap, >= 0; default 100                 */
+    int32_t score_mode;   /* CCS_SCORE_*; default CCS_SCORE_L0_DECREASE       */
+    int32_t engine;       /* CCS_ENGINE_*; default CCS_ENGINE_AUTO            */
+    int32_t watchdog_ms;  /* bound on every device-side wait; 0 = 2000 ms     */
+    int32_t reserved[3];  /* must be zero                                     */
+} ccs_params;
+
+typedef struct {
+    int32_t status;       /* CCS_CONVERGED / CCS_STALLED / CCS_MAX_ITER        */
+    int32_t iterations;   /* completed iterations (each one: score all
+                             columns, apply, recompute r)                    */
+    int64_t r0_final;     /* ||r||_0 at exit                                   */
+    int32_t error;        /* CCS_OK, or the CCS_E* code that ended this
+                             problem early (e.g. CCS_ETIMEOUT)               */
+    int32_t reserved;
+} ccs_result;
+
+/* One problem of a batch: sizes and caller-owned device arrays. */
+typedef struct {
+    int32_t n, m, d, reserved;
+    const int32_t *csc_rows;  /* n*d                                         */
+    const int64_t *csr_ptr;   /* m+1                                         */
+    const int32_t *csr_cols;  /* n*d                                         */
+    const double *y;          /* m                                           */
+    double *x_hat;            /* out, n                                      */
+    double *r;                /* out, m: y - A x_hat at exit                 */
+    int64_t *r0_hist;         /* optional out, max_iter+1 entries (NULL: off) */
+} ccs_problem;
+
+/* Workspace sizes (bytes) for the calls below. */
+enum { CCS_OP_MAKE_EXPANDER = 0, CCS_OP_DECODE = 1 };
+
+/* Fills *p with the defaults listed in ccs_params. */
+CCS_API void ccs_params_init(ccs_params *p);
+
+/* Human-readable name of a status code (static string). */
+CCS_API const char *ccs_status_string(int status);
+
+/* Description of the calling thread's last failed call (static per thread). */
+CCS_API const char *ccs_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+CCS_API int ccs_version(void);
+
+/* Bytes of workspace that ccs_make_expander (op = CCS_OP_MAKE_EXPANDER) or
+ * ccs_decode_parallel_l0 (op = CCS_OP_DECODE) needs for these sizes;
+ * 0 if the sizes are invalid. */
+CCS_API size_t ccs_workspace_size(int32_t op, int32_t n, int32_t m, int32_t d);
+
+/* Bytes of workspace that ccs_decode_batch needs for these problems. */
+CCS_API size_t ccs_batch_workspace_size(const ccs_problem *probs, int32_t count);
+
+/*
+ * ccs_make_expander -- draw a random left d-regular expander and its
+ * transpose (Sec. 1.1 footnote: columns iid, each column's support uniform
+ * over the C(m, d) subsets of size d; Table 1: O(dn) generation).
+ *
+ * Column j takes the SplitMix64 stream (Steele, Lea & Flood 2014) that
+ * starts at seed + (j+1) * 0xd1b54a32d192ed03 mod 2^64, maps each draw to a
+ * row with Lemire's bounded method (ACM TOMACS 2019), redraws repeated rows
+ * and sorts its d rows.  The result depends only on (n, m, d, seed).
+ *
+ * out: csc_rows[n*d], csr_ptr[m+1], csr_cols[n*d] (device).
+ * Synchronises the stream.  CCS_EINVAL if the sizes break the limits or a
+ * row ends up with more than 32768 columns (rows are sorted on chip).
+ */
+CCS_API int ccs_make_expander(int32_t n, int32_t m, int32_t d, uint64_t seed,
+                      int32_t *csc_rows, int64_t *csr_ptr, int32_t *csr_cols,
+                      void *ws, size_t ws_bytes, ccs_stream_t stream);
+
+/*
+ * ccs_measure -- y = A x (Sec. 1, problem statement): y_i is the sum of
+ * x_j over j in N(i) in ascending j, from +0.0, zero x_j skipped.
+ * in: csr_ptr, csr_cols, x[n]; out: y[m] (device).  Asynchronous.
+ */
+CCS_API int ccs_measure(int32_t n, int32_t m, int32_t d, const int64_t *csr_ptr,
+                const int32_t *csr_cols, const double *x, double *y,
+                ccs_stream_t stream);
+
+/*
+ * ccs_decode_parallel_l0 -- Parallel-l0 (Alg. 2).
+ *
+ *   x_hat <- 0, r <- y
+ *   while not converged:
+ *     for every column j, reading the same r: omega_j = the most frequent
+ *       nonzero value of r on N(j) (ties: the smallest), accepted when its
+ *       score (Eq. (15) or Alg. 8, see score_mode) is >= alpha
+ *     x_hat_j <- x_hat_j + omega_j for all accepted j at once
+ *     r <- y - A x_hat, ||r||_0
+ *
+ * "Converged" is read as: stop when ||r||_0 == 0 (CCS_CONVERGED), when no
+ * pair is accepted (CCS_STALLED; the iteration is deterministic so nothing
+ * would change again) or after max_iter iterations (CCS_MAX_ITER).
+ *
+ * in:  csc_rows, csr_ptr, csr_cols, y (device)
+ * out: x_hat[n], r[m] (device); r0_hist[max_iter+1] (device, optional:
+ *      entry t = ||r||_0 after t iterations, entries past the last
+ *      iteration untouched); *out (host memory).
+ * p may be NULL (defaults).  Blocks until the decode has finished.
+ * Errors: CCS_EINVAL (sizes, alpha outside [2, d], bad params),
+ * CCS_ENOMEM (ws_bytes too small), CCS_ECUDA, CCS_ETIMEOUT.
+ */
+CCS_API int ccs_decode_parallel_l0(int32_t n, int32_t m, int32_t d,
+                           const int32_t *csc_rows, const int64_t *csr_ptr,
+                           const int32_t *csr_cols, const double *y,
+                           double *x_hat, double *r, int64_t *r0_hist,
+                           const ccs_params *p, ccs_result *out,
+                           void *ws, size_t ws_bytes, ccs_stream_t stream);
+
+/*
+ * ccs_decode_batch -- Parallel-l0 on `count` independent problems of any
+ * sizes in one persistent cooperative launch (the iteration loop runs on the
+ * device; each problem stops on its own rule and drops out of later
+ * phases).  Per problem, the results are bit-identical to
+ * ccs_decode_parallel_l0 on that problem alone.
+ *
+ * probs: host array of `count` descriptors (device pointers inside);
+ * out: host array of `count` results.  Blocks until every problem has
+ * finished.  Errors as for ccs_decode_parallel_l0.
+ */
+CCS_API int ccs_decode_batch(const ccs_problem *probs, int32_t count,
+                     const ccs_params *p, ccs_result *out,
+                     void *ws, size_t ws_bytes, ccs_stream_t stream);
+
+/* ---- measurement hooks ---------------------------------------------------
+ * Kernel timing for benchmarks: between ccs_profile_begin() and
+ * ccs_profile_end() the library brackets each of its kernel launches with
+ * CUDA events on the launching stream and sums the elapsed device time per
+ * kernel kind.  Off by default (no events are recorded when off).  Process-
+ * wide; not meant to be used from several threads at once. */
+enum {
+    CCS_K_INIT = 0,        /* x_hat <- 0, r <- y, ||y||_0                   */
+    CCS_K_SCORE = 1,       /* score + apply (all columns)                   */
+    CCS_K_RESIDUAL = 2,    /* r on touched rows + ||r||_0                    */
+    CCS_K_FINISH = 3,      /* stop rule                                      */
+    CCS_K_PERSISTENT = 4,  /* whole decode in one cooperative launch         */
+    CCS_K_COUNT = 8
+};
+typedef struct {
+    int64_t launches;
+    double total_ms;
+} ccs_kernel_time;
+
+CCS_API int ccs_profile_begin(void);
+/* times: array of CCS_K_COUNT entries (host). */
+CCS_API int ccs_profile_end(ccs_kernel_time *times);
+/* Number of kernels this library has launched since it was loaded. */
+CCS_API int64_t ccs_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCS_H */

@@ -1,0 +1,307 @@
+"""Thin ctypes binding of libccs (include/ccs.h).
+
+Argument marshalling only: every step of the decode runs in the CUDA
+library.  PyTorch supplies device memory (tensors) and the stream.  If the
+library is missing, importing works but every call raises: there is no CPU
+fallback.
+
+The ``ccs_*`` functions mirror the C ABI one to one (tensors stand in for
+device pointers).  ``make_expander``, ``measure``, ``decode_parallel_l0`` and
+``decode_batch`` are conveniences that allocate outputs and workspaces with
+torch and call the ``ccs_*`` functions.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libccs.so")
+
+CCS_OK, CCS_EINVAL, CCS_ENOMEM, CCS_ECUDA, CCS_ETIMEOUT, CCS_EBUDGET, CCS_EBUSY = range(7)
+CONVERGED, STALLED, MAX_ITER = 0, 1, 2
+STATUS_NAMES = {CONVERGED: "converged", STALLED: "stalled", MAX_ITER: "max_iter"}
+SCORE_L0_DECREASE, SCORE_COUNT = 0, 1
+ENGINE_AUTO, ENGINE_HOST_LOOP, ENGINE_GRAPH, ENGINE_PERSISTENT = 0, 1, 2, 3
+OP_MAKE_EXPANDER, OP_DECODE = 0, 1
+
+
+class CcsError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        super().__init__(f"{where}: {_STATUS.get(code, code)}: {detail}")
+        self.code = code
+
+
+_STATUS = {0: "CCS_OK", 1: "CCS_EINVAL", 2: "CCS_ENOMEM", 3: "CCS_ECUDA",
+           4: "CCS_ETIMEOUT", 5: "CCS_EBUDGET", 6: "CCS_EBUSY"}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("score_mode", ctypes.c_int32), ("engine", ctypes.c_int32),
+                ("watchdog_ms", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("r0_final", ctypes.c_int64), ("error", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32), ("d", ctypes.c_int32),
+                ("reserved", ctypes.c_int32),
+                ("csc_rows", ctypes.c_void_p), ("csr_ptr", ctypes.c_void_p),
+                ("csr_cols", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("x_hat", ctypes.c_void_p), ("r", ctypes.c_void_p),
+                ("r0_hist", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+K_INIT, K_SCORE, K_RESIDUAL, K_FINISH, K_PERSISTENT, K_COUNT = 0, 1, 2, 3, 4, 8
+KERNEL_NAMES = {K_INIT: "init", K_SCORE: "score", K_RESIDUAL: "residual",
+                K_FINISH: "finish", K_PERSISTENT: "persistent"}
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+def lib() -> ctypes.CDLL:
+    """Load libccs.so (built in-tree by ``paper_1508_01256_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_1508_01256_gb300.build`")
+        l = ctypes.CDLL(LIB_PATH)
+        P, i32, i64, u64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                ctypes.c_uint64, ctypes.c_size_t)
+        l.ccs_params_init.argtypes = [ctypes.POINTER(Params)]
+        l.ccs_params_init.restype = None
+        l.ccs_status_string.argtypes = [ctypes.c_int]
+        l.ccs_status_string.restype = ctypes.c_char_p
+        l.ccs_last_error.argtypes = []
+        l.ccs_last_error.restype = ctypes.c_char_p
+        l.ccs_version.restype = ctypes.c_int
+        l.ccs_workspace_size.argtypes = [i32, i32, i32, i32]
+        l.ccs_workspace_size.restype = sz
+        l.ccs_batch_workspace_size.argtypes = [ctypes.POINTER(Problem), i32]
+        l.ccs_batch_workspace_size.restype = sz
+        l.ccs_make_expander.argtypes = [i32, i32, i32, u64, P, P, P, P, sz, P]
+        l.ccs_measure.argtypes = [i32, i32, i32, P, P, P, P, P]
+        l.ccs_decode_parallel_l0.argtypes = [i32, i32, i32, P, P, P, P, P, P, P,
+                                             ctypes.POINTER(Params), ctypes.POINTER(Result),
+                                             P, sz, P]
+        l.ccs_decode_batch.argtypes = [ctypes.POINTER(Problem), i32, ctypes.POINTER(Params),
+                                       ctypes.POINTER(Result), P, sz, P]
+        l.ccs_profile_begin.argtypes = []
+        l.ccs_profile_end.argtypes = [ctypes.POINTER(KernelTime)]
+        l.ccs_launch_count.argtypes = []
+        l.ccs_launch_count.restype = ctypes.c_int64
+        for name in ("ccs_make_expander", "ccs_measure", "ccs_decode_parallel_l0",
+                     "ccs_decode_batch", "ccs_profile_begin", "ccs_profile_end"):
+            getattr(l, name).restype = ctypes.c_int
+        _lib = l
+        return l
+
+
+def _check(rc: int, where: str):
+    if rc != CCS_OK:
+        raise CcsError(rc, where, lib().ccs_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _need(t, dtype, numel, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{name}: need contiguous {dtype} with {numel} elements, "
+                         f"got {t.dtype} {tuple(t.shape)}")
+
+
+def params(alpha=2, max_iter=100, score_mode=SCORE_L0_DECREASE, engine=ENGINE_AUTO,
+           watchdog_ms=0) -> Params:
+    p = Params()
+    lib().ccs_params_init(ctypes.byref(p))
+    p.alpha, p.max_iter, p.score_mode, p.engine, p.watchdog_ms = (
+        alpha, max_iter, score_mode, engine, watchdog_ms)
+    return p
+
+
+# ---- one-to-one ABI calls ---------------------------------------------------
+
+def ccs_workspace_size(op: int, n: int, m: int, d: int) -> int:
+    return int(lib().ccs_workspace_size(op, n, m, d))
+
+
+def ccs_batch_workspace_size(probs) -> int:
+    arr = (Problem * len(probs))(*probs)
+    return int(lib().ccs_batch_workspace_size(arr, len(probs)))
+
+
+def ccs_make_expander(n, m, d, seed, csc_rows, csr_ptr, csr_cols, ws, stream=None):
+    _check(lib().ccs_make_expander(n, m, d, seed & (2**64 - 1), _ptr(csc_rows),
+                                   _ptr(csr_ptr), _ptr(csr_cols), _ptr(ws),
+                                   ws.numel() * ws.element_size(), _stream(stream)),
+           "ccs_make_expander")
+
+
+def ccs_measure(n, m, d, csr_ptr, csr_cols, x, y, stream=None):
+    _check(lib().ccs_measure(n, m, d, _ptr(csr_ptr), _ptr(csr_cols), _ptr(x), _ptr(y),
+                             _stream(stream)), "ccs_measure")
+
+
+def ccs_decode_parallel_l0(n, m, d, csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist,
+                           p: Params | None, ws, stream=None) -> Result:
+    out = Result()
+    rc = lib().ccs_decode_parallel_l0(
+        n, m, d, _ptr(csc_rows), _ptr(csr_ptr), _ptr(csr_cols), _ptr(y), _ptr(x_hat), _ptr(r),
+        _ptr(r0_hist), ctypes.byref(p) if p is not None else None, ctypes.byref(out),
+        _ptr(ws), ws.numel() * ws.element_size(), _stream(stream))
+    _check(rc, "ccs_decode_parallel_l0")
+    return out
+
+
+def ccs_decode_batch(probs, p: Params | None, ws, stream=None) -> list[Result]:
+    cnt = len(probs)
+    arr = (Problem * cnt)(*probs)
+    outs = (Result * cnt)()
+    rc = lib().ccs_decode_batch(arr, cnt, ctypes.byref(p) if p is not None else None, outs,
+                                _ptr(ws), ws.numel() * ws.element_size(), _stream(stream))
+    _check(rc, "ccs_decode_batch")
+    return list(outs)
+
+
+def ccs_profile_begin():
+    _check(lib().ccs_profile_begin(), "ccs_profile_begin")
+
+
+def ccs_profile_end() -> dict:
+    """{kernel name: (launches, total_ms)} for the kernels timed since begin."""
+    arr = (KernelTime * K_COUNT)()
+    _check(lib().ccs_profile_end(arr), "ccs_profile_end")
+    return {KERNEL_NAMES.get(k, str(k)): (int(arr[k].launches), float(arr[k].total_ms))
+            for k in range(K_COUNT) if arr[k].launches}
+
+
+def ccs_launch_count() -> int:
+    return int(lib().ccs_launch_count())
+
+
+# ---- conveniences -------------------------------------------------------------
+
+def workspace(nbytes: int, device="cuda"):
+    import torch
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def make_expander(n: int, m: int, d: int, seed: int, device="cuda", stream=None):
+    """(csc_rows[n, d] int32, csr_ptr[m+1] int64, csr_cols[n*d] int32) on device."""
+    import torch
+    csc = torch.empty((n, d), dtype=torch.int32, device=device)
+    ptr = torch.empty(m + 1, dtype=torch.int64, device=device)
+    cols = torch.empty(n * d, dtype=torch.int32, device=device)
+    ws = workspace(ccs_workspace_size(OP_MAKE_EXPANDER, n, m, d), device)
+    ccs_make_expander(n, m, d, seed, csc, ptr, cols, ws, stream)
+    return csc, ptr, cols
+
+
+def measure(csr_ptr, csr_cols, x, m: int, d: int, stream=None):
+    import torch
+    n = x.numel()
+    _need(csr_ptr, torch.int64, m + 1, "csr_ptr")
+    _need(csr_cols, torch.int32, n * d, "csr_cols")
+    _need(x, torch.float64, n, "x")
+    y = torch.empty(m, dtype=torch.float64, device=x.device)
+    ccs_measure(n, m, d, csr_ptr, csr_cols, x, y, stream)
+    return y
+
+
+class DecodeOutput(dict):
+    __getattr__ = dict.__getitem__
+
+
+def decode_parallel_l0(csc_rows, csr_ptr, csr_cols, y, alpha=2, max_iter=100,
+                       score_mode=SCORE_L0_DECREASE, engine=ENGINE_AUTO, history=True,
+                       ws=None, out=None, stream=None) -> DecodeOutput:
+    """Parallel-l0 (Alg. 2) on one problem; returns x_hat, r (device tensors),
+    r0_hist (host list), status, iterations, r0_final."""
+    import torch
+    n, d = csc_rows.shape
+    m = y.numel()
+    _need(csc_rows, torch.int32, n * d, "csc_rows")
+    _need(csr_ptr, torch.int64, m + 1, "csr_ptr")
+    _need(csr_cols, torch.int32, n * d, "csr_cols")
+    _need(y, torch.float64, m, "y")
+    dev = y.device
+    if out is None:
+        x_hat = torch.empty(n, dtype=torch.float64, device=dev)
+        r = torch.empty(m, dtype=torch.float64, device=dev)
+        hist = torch.full((max_iter + 1,), -1, dtype=torch.int64, device=dev) if history else None
+    else:
+        x_hat, r, hist = out
+    if ws is None:
+        ws = workspace(ccs_workspace_size(OP_DECODE, n, m, d), dev)
+    p = params(alpha, max_iter, score_mode, engine)
+    res = ccs_decode_parallel_l0(n, m, d, csc_rows, csr_ptr, csr_cols, y, x_hat, r, hist, p,
+                                 ws, stream)
+    h = hist[:res.iterations + 1].cpu().tolist() if hist is not None else None
+    return DecodeOutput(x_hat=x_hat, r=r, r0_hist=h, status=res.status,
+                        iterations=res.iterations, r0_final=res.r0_final, error=res.error)
+
+
+def problem(csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist=None) -> Problem:
+    n, d = csc_rows.shape
+    return Problem(n, y.numel(), d, 0, _ptr(csc_rows), _ptr(csr_ptr), _ptr(csr_cols),
+                   _ptr(y), _ptr(x_hat), _ptr(r), _ptr(r0_hist))
+
+
+def decode_batch(items, alpha=2, max_iter=100, score_mode=SCORE_L0_DECREASE,
+                 engine=ENGINE_AUTO, history=False, ws=None, stream=None):
+    """items: list of (csc_rows, csr_ptr, csr_cols, y).  Returns a list of
+    DecodeOutput, one per problem, from a single ccs_decode_batch call."""
+    import torch
+    probs, outs = [], []
+    for csc, ptr, cols, y in items:
+        n, d = csc.shape
+        m = y.numel()
+        x_hat = torch.empty(n, dtype=torch.float64, device=y.device)
+        r = torch.empty(m, dtype=torch.float64, device=y.device)
+        hist = torch.full((max_iter + 1,), -1, dtype=torch.int64, device=y.device) \
+            if history else None
+        outs.append((x_hat, r, hist))
+        probs.append(problem(csc, ptr, cols, y, x_hat, r, hist))
+    if ws is None:
+        ws = workspace(ccs_batch_workspace_size(probs), items[0][3].device)
+    p = params(alpha, max_iter, score_mode, engine)
+    res = ccs_decode_batch(probs, p, ws, stream)
+    result = []
+    for (x_hat, r, hist), rr in zip(outs, res):
+        h = hist[:rr.iterations + 1].cpu().tolist() if hist is not None else None
+        result.append(DecodeOutput(x_hat=x_hat, r=r, r0_hist=h, status=rr.status,
+                                   iterations=rr.iterations, r0_final=rr.r0_final,
+                                   error=rr.error))
+    return result

@@ -1,0 +1,312 @@
+// ccs_decode.cu -- the Parallel-l0 iteration (Alg. 2) on one problem.
+//
+// One iteration is two kernels:
+//   score   every column j reads r on its d rows (held in registers), finds
+//           the most frequent nonzero value omega_j (ties: the smallest),
+//           scores it (Eq. (15): c_omega - c_0, or Alg. 8: c_omega) and, if
+//           accepted, applies x_hat_j += omega_j at once (each column owns
+//           its x_hat_j, so the updates of one iteration do not interact).
+//           It also marks the rows N(j) as touched and, the first time a
+//           column becomes nonzero, enters j in the contributor slots of its
+//           rows.
+//   residual every touched row recomputes r_i = y_i - sum over its nonzero
+//           x_hat_j in ascending j, from +0.0.  Rows not touched keep r_i:
+//           none of their columns changed, so the same ordered sum would
+//           give the same bits.  The change of ||r||_0 is summed exactly in
+//           integers.
+// A one-thread kernel then applies the stop rule (||r||_0 == 0, nothing
+// accepted, or max_iter) and records ||r||_0.
+#include "ccs_internal.cuh"
+
+namespace ccs {
+
+// ---- init --------------------------------------------------------------
+
+__global__ void k_init(ProblemDev P) {
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long nz = 0;
+    for (long long j = tid; j < P.n; j += stride) {
+        P.x_hat[j] = 0.0;
+        P.in_slots[j] = 0;
+    }
+    for (long long i = tid; i < P.m; i += stride) {
+        const double v = P.y[i];
+        P.r[i] = v;
+        P.touched[i] = 0;
+        P.slot_cnt[i] = 0;
+        nz += (v != 0.0);
+    }
+    nz = warp_sum_ll(nz);
+    if ((threadIdx.x & 31) == 0 && nz) atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0),
+                                                 (unsigned long long)nz);
+}
+
+__global__ void k_init_finish(ProblemDev P, int max_iter) {
+    DecodeCtrl *c = P.ctrl;
+    c->iteration = 0;
+    c->max_iter = max_iter;
+    c->accepted = 0;
+    c->r0_delta = 0;
+    if (P.r0_hist) P.r0_hist[0] = c->r0;
+    c->status = (c->r0 == 0) ? CCS_CONVERGED : (max_iter == 0 ? CCS_MAX_ITER : kRunning);
+}
+
+// ---- score + apply ------------------------------------------------------
+
+template <int D>
+__device__ __forceinline__ bool score_column(const ProblemDev &P, int j, int alpha, int mode) {
+    const int32_t *rows = P.csc_rows + (size_t)j * D;
+    int rw[D];
+    unsigned long long v[D];
+#pragma unroll
+    for (int t = 0; t < D; ++t) rw[t] = __ldg(rows + t);
+#pragma unroll
+    for (int t = 0; t < D; ++t) v[t] = value_bits(P.r[rw[t]]);
+    int c0 = 0;
+#pragma unroll
+    for (int t = 0; t < D; ++t) c0 += (v[t] == 0ull);
+    int best_cnt = 0;
+    unsigned long long best_bits = 0ull, best_key = ~0ull;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        int c = 0;
+#pragma unroll
+        for (int b = 0; b < D; ++b) c += (v[b] == v[a]);
+        const unsigned long long key = order_key(v[a]);
+        const bool better = (v[a] != 0ull) && (c > best_cnt || (c == best_cnt && key < best_key));
+        best_cnt = better ? c : best_cnt;
+        best_key = better ? key : best_key;
+        best_bits = better ? v[a] : best_bits;
+    }
+    const int score = (mode == CCS_SCORE_COUNT) ? best_cnt : best_cnt - c0;
+    const bool accept = best_cnt > 0 && score >= alpha;
+    if (accept) {
+        const double omega = __longlong_as_double((long long)best_bits);
+        P.x_hat[j] = __dadd_rn(P.x_hat[j], omega);
+#pragma unroll
+        for (int t = 0; t < D; ++t) P.touched[rw[t]] = 1;
+        if (!P.in_slots[j]) {
+            P.in_slots[j] = 1;
+#pragma unroll
+            for (int t = 0; t < D; ++t) {
+                const int pos = atomicAdd(&P.slot_cnt[rw[t]], 1);
+                if (pos < kSlots) P.slots[(size_t)rw[t] * kSlots + pos] = j;
+            }
+        }
+    }
+    return accept;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_score(ProblemDev P, int alpha, int mode) {
+    if (ld_volatile(&P.ctrl->status) != kRunning) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    bool acc = false;
+    if (j < P.n) acc = score_column<D>(P, j, alpha, mode);
+    const unsigned bal = __ballot_sync(0xffffffffu, acc);
+    if ((threadIdx.x & 31) == 0 && bal)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->accepted),
+                  (unsigned long long)__popc(bal));
+}
+
+// ---- residual + ||r||_0 ---------------------------------------------------
+
+// r_i = y_i - (sum of nonzero x_hat_j, j in N(i), ascending), for one row.
+__device__ __forceinline__ double row_residual(const ProblemDev &P, int i) {
+    const int cnt = P.slot_cnt[i];
+    double s = 0.0;
+    if (cnt <= kSlots) {
+        // The row's contributors are the columns in its slots (every column
+        // with x_hat_j != 0 entered them when it first became nonzero); visit
+        // them in ascending j by repeated minimum selection.
+        const int32_t *sl = P.slots + (size_t)i * kSlots;
+        int js[kSlots];
+#pragma unroll
+        for (int q = 0; q < kSlots; ++q) js[q] = (q < cnt) ? sl[q] : 0x7fffffff;
+        int last = -1;
+        for (int step = 0; step < cnt; ++step) {
+            int nxt = 0x7fffffff;
+#pragma unroll
+            for (int q = 0; q < kSlots; ++q) nxt = (js[q] > last && js[q] < nxt) ? js[q] : nxt;
+            last = nxt;
+            const double v = P.x_hat[nxt];
+            if (v != 0.0) s = __dadd_rn(s, v);
+        }
+    } else {
+        // More contributors than slots: walk the whole CSR row.
+        for (int64_t p = P.csr_ptr[i]; p < P.csr_ptr[i + 1]; ++p) {
+            const double v = P.x_hat[P.csr_cols[p]];
+            if (v != 0.0) s = __dadd_rn(s, v);
+        }
+    }
+    return __dsub_rn(P.y[i], s);
+}
+
+__global__ void __launch_bounds__(256) k_residual(ProblemDev P) {
+    if (ld_volatile(&P.ctrl->status) != kRunning) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    long long delta = 0;
+    if (i < P.m && P.touched[i]) {
+        P.touched[i] = 0;
+        const double rn = row_residual(P, i);
+        const double ro = P.r[i];
+        delta = (long long)(rn != 0.0) - (long long)(ro != 0.0);
+        P.r[i] = rn;
+    }
+    delta = warp_sum_ll(delta);
+    if ((threadIdx.x & 31) == 0 && delta)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0_delta),
+                  (unsigned long long)delta);
+}
+
+// ---- stop rule --------------------------------------------------------------
+
+__global__ void k_finish(ProblemDev P) {
+    DecodeCtrl *c = P.ctrl;
+    if (c->status != kRunning) return;
+    if (c->accepted == 0) {
+        c->status = CCS_STALLED;
+        return;
+    }
+    c->iteration += 1;
+    c->r0 += c->r0_delta;
+    c->accepted = 0;
+    c->r0_delta = 0;
+    if (P.r0_hist) P.r0_hist[c->iteration] = c->r0;
+    if (c->r0 == 0) c->status = CCS_CONVERGED;
+    else if (c->iteration >= c->max_iter) c->status = CCS_MAX_ITER;
+}
+
+// ---- dispatch ----------------------------------------------------------------
+
+typedef void (*score_fn)(ProblemDev, int, int);
+
+static score_fn score_kernel(int d) {
+    switch (d) {
+        case 1: return k_score<1>;
+        case 2: return k_score<2>;
+        case 3: return k_score<3>;
+        case 4: return k_score<4>;
+        case 5: return k_score<5>;
+        case 6: return k_score<6>;
+        case 7: return k_score<7>;
+        case 8: return k_score<8>;
+        case 9: return k_score<9>;
+        case 10: return k_score<10>;
+        case 11: return k_score<11>;
+        case 12: return k_score<12>;
+        case 13: return k_score<13>;
+        case 14: return k_score<14>;
+        case 15: return k_score<15>;
+        case 16: return k_score<16>;
+        default: return nullptr;
+    }
+}
+
+int check_params(const ccs_params *p, int d) {
+    if (p->alpha < 2 || p->alpha > d) {
+        set_last_error("alpha=%d outside [2, d=%d]", p->alpha, d);
+        return CCS_EINVAL;
+    }
+    if (p->max_iter < 0) {
+        set_last_error("max_iter=%d < 0", p->max_iter);
+        return CCS_EINVAL;
+    }
+    if (p->score_mode != CCS_SCORE_L0_DECREASE && p->score_mode != CCS_SCORE_COUNT) {
+        set_last_error("unknown score_mode %d", p->score_mode);
+        return CCS_EINVAL;
+    }
+    if (p->engine < CCS_ENGINE_AUTO || p->engine > CCS_ENGINE_PERSISTENT) {
+        set_last_error("unknown engine %d", p->engine);
+        return CCS_EINVAL;
+    }
+    if (p->watchdog_ms < 0 || p->reserved[0] || p->reserved[1] || p->reserved[2]) {
+        set_last_error("bad watchdog_ms or nonzero reserved fields");
+        return CCS_EINVAL;
+    }
+    return CCS_OK;
+}
+
+// Host-driven loop: one score, residual and stop-rule launch per iteration,
+// then a 64-byte read of the control block to decide whether to go on.
+static int decode_host_loop(const ProblemDev &P, const ccs_params &p, ccs_result *out,
+                            cudaStream_t s) {
+    score_fn score = score_kernel(P.d);
+    const int nb_cols = (P.n + 255) / 256, nb_rows = (P.m + 255) / 256;
+    const long long big = P.n > P.m ? P.n : P.m;
+    const int nb_init = (int)((big + 255) / 256 < 152 * 16 ? (big + 255) / 256 : 152 * 16);
+    CCS_CUDA_TRY(cudaMemsetAsync(P.ctrl, 0, sizeof(DecodeCtrl), s));
+    int ev = prof_start(CCS_K_INIT, s);
+    k_init<<<nb_init, 256, 0, s>>>(P);
+    prof_stop(ev, s);
+    k_init_finish<<<1, 1, 0, s>>>(P, p.max_iter);
+    count_launches(2);
+    CCS_CUDA_TRY(cudaGetLastError());
+    DecodeCtrl h;
+    CCS_CUDA_TRY(cudaMemcpyAsync(&h, P.ctrl, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CCS_CUDA_TRY(cudaStreamSynchronize(s));
+    while (h.status == kRunning) {
+        ev = prof_start(CCS_K_SCORE, s);
+        score<<<nb_cols, 256, 0, s>>>(P, p.alpha, p.score_mode);
+        prof_stop(ev, s);
+        ev = prof_start(CCS_K_RESIDUAL, s);
+        k_residual<<<nb_rows, 256, 0, s>>>(P);
+        prof_stop(ev, s);
+        ev = prof_start(CCS_K_FINISH, s);
+        k_finish<<<1, 1, 0, s>>>(P);
+        prof_stop(ev, s);
+        count_launches(3);
+        CCS_CUDA_TRY(cudaGetLastError());
+        CCS_CUDA_TRY(cudaMemcpyAsync(&h, P.ctrl, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CCS_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    if (profiling()) prof_collect();
+    out->status = h.status;
+    out->iterations = h.iteration;
+    out->r0_final = h.r0;
+    out->error = (h.error & kErrWatchdog) ? CCS_ETIMEOUT : CCS_OK;
+    out->reserved = 0;
+    return out->error;
+}
+
+}  // namespace ccs
+
+using namespace ccs;
+
+extern "C" int ccs_decode_parallel_l0(int32_t n, int32_t m, int32_t d, const int32_t *csc_rows,
+                                      const int64_t *csr_ptr, const int32_t *csr_cols,
+                                      const double *y, double *x_hat, double *r,
+                                      int64_t *r0_hist, const ccs_params *params,
+                                      ccs_result *out, void *ws, size_t ws_bytes,
+                                      ccs_stream_t stream) {
+    int rc = check_sizes(n, m, d);
+    if (rc) return rc;
+    ccs_params p;
+    if (params) p = *params;
+    else ccs_params_init(&p);
+    if ((rc = check_params(&p, d))) return rc;
+    if (!csc_rows || !csr_ptr || !csr_cols || !y || !x_hat || !r || !out || !ws) {
+        set_last_error("ccs_decode_parallel_l0: null pointer argument");
+        return CCS_EINVAL;
+    }
+    const size_t need = decode_ws_layout(n, m, nullptr, nullptr);
+    if (ws_bytes < need) {
+        set_last_error("ccs_decode_parallel_l0: workspace %zu < %zu bytes", ws_bytes, need);
+        return CCS_ENOMEM;
+    }
+    ProblemDev P{};
+    P.n = n;
+    P.m = m;
+    P.d = d;
+    P.csc_rows = csc_rows;
+    P.csr_ptr = csr_ptr;
+    P.csr_cols = csr_cols;
+    P.y = y;
+    P.x_hat = x_hat;
+    P.r = r;
+    P.r0_hist = r0_hist;
+    decode_ws_layout(n, m, &P, static_cast<char *>(ws));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return decode_host_loop(P, p, out, s);
+}

@@ -1,0 +1,121 @@
+// ccs_internal.cuh -- device helpers shared by the libccs translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ccs.h"
+
+namespace ccs {
+
+constexpr int kMaxD = 16;           // register-resident gather of d <= 16 values
+constexpr int kSlots = 16;          // contributor slots kept per row
+constexpr int kMaxSortRow = 32768;  // longest CSR row sorted on chip
+constexpr int kRunning = -1;        // DecodeCtrl::status while iterating
+
+enum ErrorBits : int {
+    kErrWatchdog = 1,
+};
+
+// Per-problem decode state kept in the workspace (device memory).
+struct alignas(64) DecodeCtrl {
+    long long r0;         // ||r||_0 after the last completed iteration
+    long long accepted;   // accepted pairs in the current iteration
+    long long r0_delta;   // change of ||r||_0 made by the current residual phase
+    int iteration;        // completed iterations
+    int status;           // kRunning or CCS_CONVERGED / _STALLED / _MAX_ITER
+    int error;            // ErrorBits
+    int max_iter;
+    int pad[6];
+};
+static_assert(sizeof(DecodeCtrl) == 64, "DecodeCtrl layout");
+
+// Device view of one problem plus its slice of the workspace.
+struct ProblemDev {
+    int n, m, d, pad;
+    const int32_t *csc_rows;
+    const int64_t *csr_ptr;
+    const int32_t *csr_cols;
+    const double *y;
+    double *x_hat;
+    double *r;
+    int64_t *r0_hist;     // may be null
+    DecodeCtrl *ctrl;
+    uint8_t *touched;     // m: rows whose sum must be recomputed
+    uint8_t *in_slots;    // n: column already entered in its rows' slots
+    int32_t *slot_cnt;    // m: columns entered in the row's slots
+    int32_t *slots;       // m * kSlots: those columns, unordered
+};
+
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Workspace carve-up of one decode problem: returns bytes used from `base`.
+__host__ inline size_t decode_ws_layout(int n, int m, ProblemDev *pd, char *base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *p = base ? base + off : nullptr;
+        off = align_up(off + bytes, 256);
+        return p;
+    };
+    char *ctrl = take(sizeof(DecodeCtrl));
+    char *touched = take((size_t)m);
+    char *in_slots = take((size_t)n);
+    char *slot_cnt = take((size_t)m * 4);
+    char *slots = take((size_t)m * kSlots * 4);
+    if (pd) {
+        pd->ctrl = reinterpret_cast<DecodeCtrl *>(ctrl);
+        pd->touched = reinterpret_cast<uint8_t *>(touched);
+        pd->in_slots = reinterpret_cast<uint8_t *>(in_slots);
+        pd->slot_cnt = reinterpret_cast<int32_t *>(slot_cnt);
+        pd->slots = reinterpret_cast<int32_t *>(slots);
+    }
+    return off;
+}
+
+// ---- binary64 bit helpers ------------------------------------------------
+
+// Bits of v with -0.0 folded onto +0.0, so that bit equality is value
+// equality for every finite double and 0 means "zero".
+__device__ __forceinline__ unsigned long long value_bits(double v) {
+    unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+    return (b << 1) == 0ull ? 0ull : b;
+}
+
+// Unsigned key with the numeric order of the (non-NaN) doubles.
+__device__ __forceinline__ unsigned long long order_key(unsigned long long b) {
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile(const int *p) {
+    return *reinterpret_cast<const volatile int *>(p);
+}
+
+// ---- host-side error reporting -------------------------------------------
+
+void set_last_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define CCS_CUDA_TRY(expr)                                        \
+    do {                                                          \
+        cudaError_t _e = (expr);                                  \
+        if (_e != cudaSuccess) return ::ccs::cuda_fail(_e, #expr); \
+    } while (0)
+
+int check_sizes(int32_t n, int32_t m, int32_t d);
+
+// launch counting / optional event timing (ccs_profile.cu)
+void count_launches(int k);
+bool profiling();
+int prof_start(int kind, cudaStream_t s);
+void prof_stop(int slot, cudaStream_t s);
+void prof_collect();
+int check_params(const ccs_params *p, int d);
+
+}  // namespace ccs

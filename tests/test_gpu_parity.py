@@ -1,0 +1,267 @@
+"""GPU parity: every output of the CUDA path, called through the C ABI, is
+bit-identical to the CPU oracle on the same seeded inputs (tolerance 0:
+both sides add in the same order in binary64 and decide equality exactly).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1508_01256_gb300 import inputs
+from gpu_util import assert_same_decode, device_problem, oracle_problem, upload_matrix
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ccs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1508_01256_gb300 import build, ccs
+    build.build()
+    return ccs
+
+
+# ---- generator, transpose, measure -----------------------------------------
+
+EXPANDER_SIZES = [(1, 1, 1), (5, 5, 5), (1000, 97, 1), (1000, 97, 2), (3001, 211, 3),
+                  (4096, 410, 7), (777, 16, 16), (20000, 1000, 11), (2 ** 20, 2 ** 17, 7),
+                  (2 ** 20, 1049, 9)]
+
+
+@pytest.mark.parametrize("n,m,d", EXPANDER_SIZES)
+def test_expander_bitwise(ccs, orc, n, m, d):
+    seed = 0x5eed0000 + n + 7 * m + d
+    csc, ptr, cols = ccs.make_expander(n, m, d, seed)
+    A = orc.make_expander(n, m, d, seed)
+    assert np.array_equal(csc.cpu().numpy(), A)
+    optr, ocols = orc.transpose(A, m)
+    assert np.array_equal(ptr.cpu().numpy(), optr)
+    assert np.array_equal(cols.cpu().numpy(), ocols)
+
+
+def test_expander_full_extreme_size(ccs, orc):
+    """n = 2^24, m = 16777, d = 9: rows of ~9000 columns sorted on chip."""
+    n, m, d = 2 ** 24, 16777, 9
+    csc, ptr, cols = ccs.make_expander(n, m, d, 99)
+    A = orc.make_expander(n, m, d, 99)
+    assert np.array_equal(csc.cpu().numpy(), A)
+    optr, ocols = orc.transpose(A, m)
+    assert np.array_equal(ptr.cpu().numpy(), optr)
+    assert np.array_equal(cols.cpu().numpy(), ocols)
+
+
+@pytest.mark.parametrize("model", ["gauss-grid", "gauss-raw", "pm1"])
+@pytest.mark.parametrize("shape", [(4096, 410, 7, 41), (2 ** 20, 2 ** 17, 7, 26214),
+                                   (100003, 1001, 9, 300)])
+def test_measure_bitwise(ccs, orc, model, shape):
+    n, m, d, k = shape
+    p = inputs.make_problem(n, m, d, k, 31 + n, model)
+    _, _, _, y = device_problem(ccs, p)
+    _, y_ref = oracle_problem(orc, p)
+    assert np.array_equal(y.cpu().numpy().view(np.int64), y_ref.view(np.int64))
+
+
+# ---- whole decodes ------------------------------------------------------------
+
+def _decode_both(ccs, orc, p, **kw):
+    csc, ptr, cols, y = device_problem(ccs, p)
+    g = ccs.decode_parallel_l0(csc, ptr, cols, y, **kw)
+    A, y_ref = oracle_problem(orc, p)
+    okw = {k: v for k, v in kw.items() if k in ("alpha", "max_iter", "score_mode")}
+    ref = orc.parallel_l0(A, p.m, y_ref, **okw)
+    return g, ref
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("model", ["gauss-grid", "gauss-raw", "pm1"])
+def test_decode_small_workload(ccs, orc, seed, model):
+    """n=4096, m=410, k=41, d=7."""
+    g, ref = _decode_both(ccs, orc, inputs.plain_small(seed=seed, model=model))
+    assert_same_decode(g, ref)
+    if model == "gauss-grid":
+        assert g.status == ccs.CONVERGED
+
+
+def test_decode_at_scale_grid(ccs, orc):
+    """n=2^20, m=2^17, k=26214, d=7: the benchmark workload, compared whole."""
+    p = inputs.plain_at_scale(seed=inputs.BASE_SEED)
+    g, ref = _decode_both(ccs, orc, p)
+    assert_same_decode(g, ref)
+    assert g.status == ccs.CONVERGED
+    assert np.array_equal(g.x_hat.cpu().numpy(), p.x)
+
+
+def test_decode_at_scale_raw(ccs, orc):
+    p = inputs.plain_at_scale(seed=3, model="gauss-raw")
+    g, ref = _decode_both(ccs, orc, p, max_iter=12)
+    assert_same_decode(g, ref)
+
+
+@pytest.mark.parametrize("rho", inputs.EXTREME_RHOS)
+def test_decode_extreme_undersampling_scaled(ccs, orc, rho):
+    """delta ~ 10^-3, d = 9 at n = 2^20 (the n = 2^24 shape scaled down)."""
+    p = inputs.extreme_undersampling(rho, d=9, seed=11, log2n=20)
+    g, ref = _decode_both(ccs, orc, p)
+    assert_same_decode(g, ref)
+
+
+def test_decode_extreme_undersampling_full(ccs, orc):
+    """n = 2^24, m = 16777, d = 9, rho = 0.05, compared whole."""
+    p = inputs.extreme_undersampling(0.05, d=9, seed=5)
+    g, ref = _decode_both(ccs, orc, p)
+    assert_same_decode(g, ref)
+    assert g.status == ccs.CONVERGED
+
+
+def test_decode_extreme_pm1(ccs, orc):
+    p = inputs.extreme_undersampling(0.05, d=9, seed=6, model="pm1", log2n=20)
+    g, ref = _decode_both(ccs, orc, p)
+    assert_same_decode(g, ref)
+
+
+@pytest.mark.parametrize("d", [2, 3, 5, 8, 11, 13, 16])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_decode_all_d_and_modes(ccs, orc, d, mode):
+    n = 6007  # not a multiple of the block size: ragged tail
+    m = max(d, 700)
+    p = inputs.make_problem(n, m, d, 70, 900 + d, "gauss-grid")
+    for alpha in sorted({2, (d + 1) // 2 + (d % 2 == 0), d}):
+        if alpha < 2:
+            continue
+        g, ref = _decode_both(ccs, orc, p, alpha=alpha, score_mode=mode, max_iter=40)
+        assert_same_decode(g, ref)
+
+
+def test_first_iteration_is_the_score_step(ccs, orc):
+    """max_iter = 1: x_hat equals omega_j on the accepted columns of one score
+    pass over r = y (Eq. (15) with the tie rule), zero elsewhere."""
+    p = inputs.plain_small(seed=4)
+    g, ref = _decode_both(ccs, orc, p, max_iter=1)
+    assert_same_decode(g, ref)
+    A, y_ref = oracle_problem(orc, p)
+    acc, om, _ = orc.score_all(A, y_ref)
+    expect = np.where(acc, om, 0.0)
+    assert np.array_equal(g.x_hat.cpu().numpy(), expect)
+
+
+def test_edge_k0(ccs, orc):
+    p = inputs.make_problem(3000, 300, 7, 0, 1)
+    g, ref = _decode_both(ccs, orc, p)
+    assert_same_decode(g, ref)
+    assert g.status == ccs.CONVERGED and g.iterations == 0
+
+
+def test_edge_max_iter_zero(ccs, orc):
+    g, ref = _decode_both(ccs, orc, inputs.plain_small(seed=1), max_iter=0)
+    assert_same_decode(g, ref)
+    assert g.status == ccs.MAX_ITER
+
+
+def test_edge_tiny_shapes(ccs, orc):
+    for (n, m, d, k) in [(1, 2, 2, 1), (2, 2, 2, 1), (7, 3, 3, 2), (33, 5, 4, 3), (257, 16, 16, 5)]:
+        p = inputs.make_problem(n, m, d, k, n * 31 + m)
+        g, ref = _decode_both(ccs, orc, p, alpha=2)
+        assert_same_decode(g, ref)
+
+
+def test_edge_stalled(ccs, orc):
+    import torch
+    A = np.array([[0, 1, 2], [2, 3, 4]], dtype=np.int32)
+    csc, ptr, cols = upload_matrix(orc, A, 5)
+    y = np.array([1.0, 2.0, 3.0, 4.0, 5.0])
+    g = ccs.decode_parallel_l0(csc, ptr, cols, torch.from_numpy(y).cuda(), alpha=2)
+    ref = orc.parallel_l0(A, 5, y)
+    assert_same_decode(g, ref)
+    assert g.status == ccs.STALLED
+
+
+def test_edge_count_mode_oscillation(ccs, orc):
+    import torch
+    A = np.array([[0, 1, 2], [0, 1, 3], [2, 3, 4]], dtype=np.int32)
+    csc, ptr, cols = upload_matrix(orc, A, 5)
+    y = np.array([0.5, 0.5, 0.5, 0.0, 0.0])
+    for mode in (0, 1):
+        g = ccs.decode_parallel_l0(csc, ptr, cols, torch.from_numpy(y).cuda(), alpha=2,
+                                   score_mode=mode, max_iter=9)
+        ref = orc.parallel_l0(A, 5, y, alpha=2, score_mode=mode, max_iter=9)
+        assert_same_decode(g, ref)
+
+
+def test_edge_slot_overflow_rows(ccs, orc):
+    """Rows with more than 16 nonzero contributors take the whole-row path."""
+    n, m, d = 4000, 60, 7   # k d / m ~ 47 contributors per row
+    p = inputs.make_problem(n, m, d, 400, 77)
+    g, ref = _decode_both(ccs, orc, p, max_iter=20)
+    assert_same_decode(g, ref)
+
+
+def _affine_plane(q):
+    lines = [sorted(a * q + (s * a + c) % q for a in range(q)) for s in range(q) for c in range(q)]
+    lines += [sorted(c * q + b for b in range(q)) for c in range(q)]
+    return np.array(lines, dtype=np.int32)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_theorem_regime_on_gpu(ccs, orc, seed):
+    """AG(2,7) incidence (eps < 1/4 for k <= 4, alpha = 4): exact recovery,
+    bit-identical to the oracle."""
+    import torch
+    rng = np.random.default_rng(seed)
+    A = _affine_plane(7)
+    perm = rng.permutation(49).astype(np.int32)
+    A = np.sort(perm[A], axis=1).astype(np.int32)
+    x = np.zeros(A.shape[0])
+    supp = rng.choice(A.shape[0], size=4, replace=False)
+    x[supp] = inputs.values(4, seed, "gauss-grid")
+    y = orc.measure(A, 49, x)
+    csc, ptr, cols = upload_matrix(orc, A, 49)
+    g = ccs.decode_parallel_l0(csc, ptr, cols, torch.from_numpy(y).cuda(), alpha=4)
+    ref = orc.parallel_l0(A, 49, y, alpha=4)
+    assert_same_decode(g, ref)
+    assert np.array_equal(g.x_hat.cpu().numpy(), x)
+
+
+def test_workspace_reuse_and_dirty_outputs(ccs, orc):
+    """A reused workspace and garbage in the output buffers change nothing."""
+    import torch
+    p = inputs.plain_small(seed=9)
+    csc, ptr, cols, y = device_problem(ccs, p)
+    ws = ccs.workspace(ccs.ccs_workspace_size(ccs.OP_DECODE, p.n, p.m, p.d))
+    ws.fill_(0xAB)
+    x_hat = torch.full((p.n,), float("nan"), dtype=torch.float64, device="cuda")
+    r = torch.full((p.m,), 3.0, dtype=torch.float64, device="cuda")
+    hist = torch.full((101,), -7, dtype=torch.int64, device="cuda")
+    A, y_ref = oracle_problem(orc, p)
+    ref = orc.parallel_l0(A, p.m, y_ref)
+    for _ in range(2):
+        g = ccs.decode_parallel_l0(csc, ptr, cols, y, ws=ws, out=(x_hat, r, hist))
+        assert_same_decode(g, ref)
+
+
+def test_batch_equals_single(ccs, orc):
+    probs = [inputs.make_problem(*shape, seed=300 + i) for i, shape in enumerate(
+        [(4096, 410, 7, 41), (1000, 100, 5, 20), (20000, 2000, 9, 400), (5000, 50, 11, 5)])]
+    items = [device_problem(ccs, p) for p in probs]
+    outs = ccs.decode_batch(items, history=True)
+    for p, (csc, ptr, cols, y), g in zip(probs, items, outs):
+        single = ccs.decode_parallel_l0(csc, ptr, cols, y)
+        assert g.status == single.status and g.iterations == single.iterations
+        assert g.r0_hist == single.r0_hist
+        assert np.array_equal(g.x_hat.cpu().numpy(), single.x_hat.cpu().numpy())
+        A, y_ref = oracle_problem(orc, p)
+        assert_same_decode(g, orc.parallel_l0(A, p.m, y_ref))
+
+
+def test_iterations_within_log_k(ccs):
+    """Sec. 5.4: iterations grow like log k (soft: <= ln k + 2 on exact
+    recovery at n = 2^20, delta = 0.1, d = 7, rho in [0.05, 0.1])."""
+    for rho in (0.05, 0.075, 0.1):
+        m = round(0.1 * 2 ** 20)
+        k = inputs.round_half_up(rho * m)
+        p = inputs.make_problem(2 ** 20, m, 7, k, 4242)
+        csc, ptr, cols, y = device_problem(ccs, p)
+        g = ccs.decode_parallel_l0(csc, ptr, cols, y)
+        assert g.status == ccs.CONVERGED
+        assert g.iterations <= math.log(k) + 2

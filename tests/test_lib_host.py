@@ -1,0 +1,97 @@
+"""Host-side checks of libccs that need no GPU: the library builds for
+sm_103a, exports every entry point that include/ccs.h declares, sizes its
+workspaces and rejects bad arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ccs():
+    from paper_1508_01256_gb300 import build, ccs
+    build.build()
+    return ccs
+
+
+def _declared():
+    names = []
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            names += re.findall(r"CCS_API\s+[\w\s\*]+?\b(ccs_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(ccs):
+    names = _declared()
+    assert len(names) >= 13
+    lib = ctypes.CDLL(ccs.LIB_PATH)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_version_and_status_strings(ccs):
+    l = ccs.lib()
+    assert l.ccs_version() >= 10000
+    assert l.ccs_status_string(0) == b"CCS_OK"
+    assert l.ccs_status_string(4) == b"CCS_ETIMEOUT"
+
+
+def test_params_defaults(ccs):
+    p = ccs.params()
+    assert (p.alpha, p.max_iter, p.score_mode, p.engine, p.watchdog_ms) == (2, 100, 0, 0, 0)
+
+
+def test_workspace_sizes(ccs):
+    a = ccs.ccs_workspace_size(ccs.OP_DECODE, 4096, 410, 7)
+    b = ccs.ccs_workspace_size(ccs.OP_DECODE, 2 ** 20, 2 ** 17, 7)
+    assert 0 < a < b
+    assert ccs.ccs_workspace_size(ccs.OP_MAKE_EXPANDER, 4096, 410, 7) > 410 * 4
+    for bad in [(0, 10, 3), (10, 0, 3), (10, 5, 0), (10, 5, 6), (10, 40, 17), (2 ** 28, 10 ** 6, 9)]:
+        assert ccs.ccs_workspace_size(ccs.OP_DECODE, *bad) == 0
+
+
+def test_batch_workspace_is_sum(ccs):
+    probs = [ccs.Problem(4096, 410, 7, 0), ccs.Problem(1000, 100, 5, 0)]
+    total = ccs.ccs_batch_workspace_size(probs)
+    assert total >= ccs.ccs_workspace_size(ccs.OP_DECODE, 4096, 410, 7) + \
+        ccs.ccs_workspace_size(ccs.OP_DECODE, 1000, 100, 5)
+
+
+def test_bad_arguments_rejected_before_device_work(ccs):
+    l = ccs.lib()
+    # sizes
+    rc = l.ccs_make_expander(10, 5, 17, 1, 1, 1, 1, 1, 1 << 20, None)
+    assert rc == ccs.CCS_EINVAL and b"d=17" in l.ccs_last_error()
+    rc = l.ccs_measure(10, 5, 6, 1, 1, 1, 1, None)
+    assert rc == ccs.CCS_EINVAL
+    # alpha outside [2, d], unknown score mode, negative max_iter
+    for kw in (dict(alpha=1), dict(alpha=8), dict(score_mode=5), dict(max_iter=-1),
+               dict(engine=9), dict(watchdog_ms=-3)):
+        p = ccs.params(**kw)
+        out = ccs.Result()
+        rc = l.ccs_decode_parallel_l0(100, 20, 7, 1, 1, 1, 1, 1, 1, None, ctypes.byref(p),
+                                      ctypes.byref(out), 1, 1 << 30, None)
+        assert rc == ccs.CCS_EINVAL, kw
+    # workspace too small
+    p = ccs.params()
+    out = ccs.Result()
+    rc = l.ccs_decode_parallel_l0(100, 20, 7, 1, 1, 1, 1, 1, 1, None, ctypes.byref(p),
+                                  ctypes.byref(out), 1, 16, None)
+    assert rc == ccs.CCS_ENOMEM and b"workspace" in l.ccs_last_error()
+    # null pointers
+    rc = l.ccs_decode_parallel_l0(100, 20, 7, None, 1, 1, 1, 1, 1, None, ctypes.byref(p),
+                                  ctypes.byref(out), 1, 1 << 30, None)
+    assert rc == ccs.CCS_EINVAL
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_1508_01256_gb300 import ccs
+    monkeypatch.setattr(ccs, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(ccs, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        ccs.lib()
