@@ -98,7 +98,9 @@ def traffic_record(kernel: str, workload_name: str):
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+    """nvidia-smi clock / throttle-reason samples (every 200 ms) from before
+    the warm-up to the end of the end-to-end loop, which brackets the timed
+    region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -291,6 +293,8 @@ def run_ccs(args):
         return ccs.decode_parallel_l0(csc, ptr, cols, y, engine=args.engine, ws=ws,
                                       out=(x_hat, r, hist))
 
+    clk = ClockSampler(local).__enter__()
+    time.sleep(0.3)  # let nvidia-smi start sampling before the GPU work
     for i in range(args.warmup):
         flush.zero_()
         decode(i)
@@ -305,18 +309,17 @@ def run_ccs(args):
     torch.cuda.synchronize()
     launches0 = ccs.ccs_launch_count()
     ccs.ccs_profile_begin()
-    with ClockSampler(local) as clk:
-        t0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.zero_()
-            evs[i][0].record(stream)
-            out = decode(i)
-            evs[i][1].record(stream)
-            iters.append(out.iterations)
-            if out.status != ccs.CONVERGED:
-                exact = False
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        out = decode(i)
+        evs[i][1].record(stream)
+        iters.append(out.iterations)
+        if out.status != ccs.CONVERGED:
+            exact = False
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
     ktimes = ccs.ccs_profile_end()
     launches = ccs.ccs_launch_count() - launches0
     if dist is not None:
@@ -352,6 +355,7 @@ def run_ccs(args):
         torch.cuda.synchronize()
         if i > 0:  # first pass is a warm-up
             e2e_t += time.perf_counter() - t1
+    clk.__exit__(None, None, None)
 
     # max over ranks
     decodes = args.steps
@@ -362,21 +366,29 @@ def run_ccs(args):
     value = world * decodes / total_s
     e2e_value = world * e2e_steps / e2e_t
 
-    # roofline of the dominant kernel (score): algorithmic bytes per launch =
-    # 4 d n (CSC row indices) + 8 m (one read of r)
-    sc_launches, sc_ms = ktimes.get("score", (0, 0.0))
-    res_launches, res_ms = ktimes.get("residual", (0, 0.0))
+    # roofline of the dominant kernel.  Algorithmic bytes of one iteration:
+    # 4 d n (every column's d row indices) + 8 m (one read of r); a decode
+    # launch moves that once per iteration.
+    per_iter = 4 * p0.d * p0.n + 8 * p0.m
     peak, peak_kind = measured_peaks()
     roof = None
-    if sc_launches:
-        bytes_per_launch = 4 * p0.d * p0.n + 8 * p0.m
-        avg_s = sc_ms / sc_launches / 1000.0
+    main = "persistent" if "persistent" in ktimes else "score"
+    launches_k, ms_k = ktimes.get(main, (0, 0.0))
+    if launches_k:
+        avg_s = ms_k / launches_k / 1000.0
+        bytes_per_launch = per_iter * (statistics.mean(iters) if main == "persistent" else 1)
         achieved = bytes_per_launch / avg_s / 1e9
-        roof = {"bound": "hbm", "kernel": "score", "achieved": achieved, "peak": peak,
+        roof = {"bound": "hbm", "kernel": main, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
-                "traffic": traffic_record("score", args.workload),
+                "traffic": traffic_record(main, args.workload),
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_us": avg_s * 1e6}
+        sc_n, sc_ms = ktimes.get("score", (0, 0.0))
+        if sc_n:
+            sc_avg = sc_ms / sc_n / 1000.0
+            roof["score_phase"] = {"achieved": per_iter / sc_avg / 1e9,
+                                   "frac": per_iter / sc_avg / 1e9 / peak,
+                                   "avg_us": sc_avg * 1e6, "count": sc_n}
     kernel_share = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in ktimes.items()}
 
     if rank == 0:
@@ -410,7 +422,7 @@ def run_ccs(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ccs", choices=["ccs", "reference"])
     ap.add_argument("--workload", default="at-scale",

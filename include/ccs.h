@@ -82,10 +82,9 @@ enum {
     CCS_ENGINE_AUTO = 0,       /* library's choice                           */
     CCS_ENGINE_HOST_LOOP = 1,  /* one launch per phase, host checks the stop
                                   rule after every iteration                 */
-    CCS_ENGINE_GRAPH = 2,      /* iteration loop in a CUDA graph with a
-                                  device-side conditional WHILE node         */
     CCS_ENGINE_PERSISTENT = 3  /* one cooperative launch runs every
-                                  iteration; grid barriers between phases    */
+                                  iteration; grid barriers between phases,
+                                  each wait bounded by watchdog_ms           */
 };
 
 typedef struct {
@@ -96,7 +95,11 @@ typedef struct {
     int32_t score_mode;   /* CCS_SCORE_*; default CCS_SCORE_L0_DECREASE       */
     int32_t engine;       /* CCS_ENGINE_*; default CCS_ENGINE_AUTO            */
     int32_t watchdog_ms;  /* bound on every device-side wait; 0 = 2000 ms     */
-    int32_t reserved[3];  /* must be zero                                     */
+    int32_t debug_flags;  /* test hooks, 0 in normal use.  Bit 0 (persistent
+                             engine): CTA 0 skips its arrival at the first
+                             score barrier, so every CTA's bounded wait runs
+                             out and the call returns CCS_ETIMEOUT           */
+    int32_t reserved[2];  /* must be zero                                     */
 } ccs_params;
 
 typedef struct {
@@ -227,7 +230,11 @@ enum {
     CCS_K_SCORE = 1,       /* score + apply (all columns)                   */
     CCS_K_RESIDUAL = 2,    /* r on touched rows + ||r||_0                    */
     CCS_K_FINISH = 3,      /* stop rule                                      */
-    CCS_K_PERSISTENT = 4,  /* whole decode in one cooperative launch         */
+    CCS_K_PERSISTENT = 4,  /* whole decode in one cooperative launch; its
+                              score and residual phases are also reported
+                              under CCS_K_SCORE / CCS_K_RESIDUAL (device
+                              timer between grid barriers, one entry per
+                              iteration)                                    */
     CCS_K_COUNT = 8
 };
 typedef struct {

@@ -23,7 +23,7 @@ CCS_OK, CCS_EINVAL, CCS_ENOMEM, CCS_ECUDA, CCS_ETIMEOUT, CCS_EBUDGET, CCS_EBUSY 
 CONVERGED, STALLED, MAX_ITER = 0, 1, 2
 STATUS_NAMES = {CONVERGED: "converged", STALLED: "stalled", MAX_ITER: "max_iter"}
 SCORE_L0_DECREASE, SCORE_COUNT = 0, 1
-ENGINE_AUTO, ENGINE_HOST_LOOP, ENGINE_GRAPH, ENGINE_PERSISTENT = 0, 1, 2, 3
+ENGINE_AUTO, ENGINE_HOST_LOOP, ENGINE_PERSISTENT = 0, 1, 3
 OP_MAKE_EXPANDER, OP_DECODE = 0, 1
 
 
@@ -40,7 +40,8 @@ _STATUS = {0: "CCS_OK", 1: "CCS_EINVAL", 2: "CCS_ENOMEM", 3: "CCS_ECUDA",
 class Params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("score_mode", ctypes.c_int32), ("engine", ctypes.c_int32),
-                ("watchdog_ms", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("watchdog_ms", ctypes.c_int32), ("debug_flags", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class Result(ctypes.Structure):
@@ -143,11 +144,11 @@ def _need(t, dtype, numel, name):
 
 
 def params(alpha=2, max_iter=100, score_mode=SCORE_L0_DECREASE, engine=ENGINE_AUTO,
-           watchdog_ms=0) -> Params:
+           watchdog_ms=0, debug_flags=0) -> Params:
     p = Params()
     lib().ccs_params_init(ctypes.byref(p))
-    p.alpha, p.max_iter, p.score_mode, p.engine, p.watchdog_ms = (
-        alpha, max_iter, score_mode, engine, watchdog_ms)
+    p.alpha, p.max_iter, p.score_mode, p.engine, p.watchdog_ms, p.debug_flags = (
+        alpha, max_iter, score_mode, engine, watchdog_ms, debug_flags)
     return p
 
 
@@ -246,7 +247,8 @@ class DecodeOutput(dict):
 
 def decode_parallel_l0(csc_rows, csr_ptr, csr_cols, y, alpha=2, max_iter=100,
                        score_mode=SCORE_L0_DECREASE, engine=ENGINE_AUTO, history=True,
-                       ws=None, out=None, stream=None) -> DecodeOutput:
+                       ws=None, out=None, stream=None, watchdog_ms=0,
+                       debug_flags=0) -> DecodeOutput:
     """Parallel-l0 (Alg. 2) on one problem; returns x_hat, r (device tensors),
     r0_hist (host list), status, iterations, r0_final."""
     import torch
@@ -265,7 +267,7 @@ def decode_parallel_l0(csc_rows, csr_ptr, csr_cols, y, alpha=2, max_iter=100,
         x_hat, r, hist = out
     if ws is None:
         ws = workspace(ccs_workspace_size(OP_DECODE, n, m, d), dev)
-    p = params(alpha, max_iter, score_mode, engine)
+    p = params(alpha, max_iter, score_mode, engine, watchdog_ms, debug_flags)
     res = ccs_decode_parallel_l0(n, m, d, csc_rows, csr_ptr, csr_cols, y, x_hat, r, hist, p,
                                  ws, stream)
     h = hist[:res.iterations + 1].cpu().tolist() if hist is not None else None

@@ -1,4 +1,4 @@
-// ccs_batch.cu -- many independent decodes per call.
+// ccs_batch.cu -- many independent decodes in one persistent launch.
 #include <vector>
 
 #include "ccs_internal.cuh"
@@ -11,7 +11,7 @@ static size_t batch_ws(const ccs_problem *probs, int32_t count) {
         if (check_sizes(probs[q].n, probs[q].m, probs[q].d) != CCS_OK) return 0;
         total += decode_ws_layout(probs[q].n, probs[q].m, nullptr, nullptr);
     }
-    return total;
+    return total + engine_ws_bytes(count);
 }
 
 }  // namespace ccs
@@ -30,21 +30,52 @@ extern "C" int ccs_decode_batch(const ccs_problem *probs, int32_t count, const c
         set_last_error("ccs_decode_batch: bad arguments");
         return CCS_EINVAL;
     }
+    ccs_params p;
+    if (params) p = *params;
+    else ccs_params_init(&p);
     const size_t need = batch_ws(probs, count);
     if (need == 0) return CCS_EINVAL;
+    int dmin = 16;
+    for (int32_t q = 0; q < count; ++q) {
+        const ccs_problem &pr = probs[q];
+        if (!pr.csc_rows || !pr.csr_ptr || !pr.csr_cols || !pr.y || !pr.x_hat || !pr.r) {
+            set_last_error("ccs_decode_batch: problem %d has a null pointer", q);
+            return CCS_EINVAL;
+        }
+        dmin = pr.d < dmin ? pr.d : dmin;
+    }
+    int rc = check_params(&p, dmin);
+    if (rc) return rc;
     if (ws_bytes < need) {
         set_last_error("ccs_decode_batch: workspace %zu < %zu bytes", ws_bytes, need);
         return CCS_ENOMEM;
     }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *base = static_cast<char *>(ws);
+    std::vector<ProblemDev> pds(count);
     for (int32_t q = 0; q < count; ++q) {
         const ccs_problem &pr = probs[q];
-        const size_t bytes = decode_ws_layout(pr.n, pr.m, nullptr, nullptr);
-        int rc = ccs_decode_parallel_l0(pr.n, pr.m, pr.d, pr.csc_rows, pr.csr_ptr, pr.csr_cols,
-                                        pr.y, pr.x_hat, pr.r, pr.r0_hist, params, &out[q], base,
-                                        bytes, stream);
-        if (rc != CCS_OK && rc != CCS_ETIMEOUT) return rc;
-        base += bytes;
+        ProblemDev &P = pds[q];
+        P = ProblemDev{};
+        P.n = pr.n;
+        P.m = pr.m;
+        P.d = pr.d;
+        P.csc_rows = pr.csc_rows;
+        P.csr_ptr = pr.csr_ptr;
+        P.csr_cols = pr.csr_cols;
+        P.y = pr.y;
+        P.x_hat = pr.x_hat;
+        P.r = pr.r;
+        P.r0_hist = pr.r0_hist;
+        base += decode_ws_layout(pr.n, pr.m, &P, base);
     }
-    return CCS_OK;
+    if (p.engine == CCS_ENGINE_HOST_LOOP) {
+        // one decode after another, each with its own launches
+        for (int32_t q = 0; q < count; ++q) {
+            rc = decode_host_loop(pds[q], p, &out[q], s);
+            if (rc != CCS_OK) return rc;
+        }
+        return CCS_OK;
+    }
+    return engine_run(pds, p, out, base, s);
 }

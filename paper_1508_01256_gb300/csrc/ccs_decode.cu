@@ -16,7 +16,7 @@
 //           integers.
 // A one-thread kernel then applies the stop rule (||r||_0 == 0, nothing
 // accepted, or max_iter) and records ||r||_0.
-#include "ccs_internal.cuh"
+#include "ccs_device.cuh"
 
 namespace ccs {
 
@@ -33,21 +33,20 @@ __global__ void k_init(ProblemDev P) {
     for (long long i = tid; i < P.m; i += stride) {
         const double v = P.y[i];
         P.r[i] = v;
+        P.fp[i] = fingerprint(v);
         P.touched[i] = 0;
         P.slot_cnt[i] = 0;
         nz += (v != 0.0);
     }
     nz = warp_sum_ll(nz);
-    if ((threadIdx.x & 31) == 0 && nz) atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0),
-                                                 (unsigned long long)nz);
+    if ((threadIdx.x & 31) == 0 && nz)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0), (unsigned long long)nz);
 }
 
 __global__ void k_init_finish(ProblemDev P, int max_iter) {
     DecodeCtrl *c = P.ctrl;
     c->iteration = 0;
     c->max_iter = max_iter;
-    c->accepted = 0;
-    c->r0_delta = 0;
     if (P.r0_hist) P.r0_hist[0] = c->r0;
     c->status = (c->r0 == 0) ? CCS_CONVERGED : (max_iter == 0 ? CCS_MAX_ITER : kRunning);
 }
@@ -55,93 +54,24 @@ __global__ void k_init_finish(ProblemDev P, int max_iter) {
 // ---- score + apply ------------------------------------------------------
 
 template <int D>
-__device__ __forceinline__ bool score_column(const ProblemDev &P, int j, int alpha, int mode) {
-    const int32_t *rows = P.csc_rows + (size_t)j * D;
-    int rw[D];
-    unsigned long long v[D];
-#pragma unroll
-    for (int t = 0; t < D; ++t) rw[t] = __ldg(rows + t);
-#pragma unroll
-    for (int t = 0; t < D; ++t) v[t] = value_bits(P.r[rw[t]]);
-    int c0 = 0;
-#pragma unroll
-    for (int t = 0; t < D; ++t) c0 += (v[t] == 0ull);
-    int best_cnt = 0;
-    unsigned long long best_bits = 0ull, best_key = ~0ull;
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        int c = 0;
-#pragma unroll
-        for (int b = 0; b < D; ++b) c += (v[b] == v[a]);
-        const unsigned long long key = order_key(v[a]);
-        const bool better = (v[a] != 0ull) && (c > best_cnt || (c == best_cnt && key < best_key));
-        best_cnt = better ? c : best_cnt;
-        best_key = better ? key : best_key;
-        best_bits = better ? v[a] : best_bits;
-    }
-    const int score = (mode == CCS_SCORE_COUNT) ? best_cnt : best_cnt - c0;
-    const bool accept = best_cnt > 0 && score >= alpha;
-    if (accept) {
-        const double omega = __longlong_as_double((long long)best_bits);
-        P.x_hat[j] = __dadd_rn(P.x_hat[j], omega);
-#pragma unroll
-        for (int t = 0; t < D; ++t) P.touched[rw[t]] = 1;
-        if (!P.in_slots[j]) {
-            P.in_slots[j] = 1;
-#pragma unroll
-            for (int t = 0; t < D; ++t) {
-                const int pos = atomicAdd(&P.slot_cnt[rw[t]], 1);
-                if (pos < kSlots) P.slots[(size_t)rw[t] * kSlots + pos] = j;
-            }
-        }
-    }
-    return accept;
-}
-
-template <int D>
 __global__ void __launch_bounds__(256) k_score(ProblemDev P, int alpha, int mode) {
     if (ld_volatile(&P.ctrl->status) != kRunning) return;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     bool acc = false;
-    if (j < P.n) acc = score_column<D>(P, j, alpha, mode);
+    if (j < P.n) {
+        int32_t rows[D];
+#pragma unroll
+        for (int t = 0; t < D; ++t) rows[t] = __ldg(P.csc_rows + (size_t)j * D + t);
+        unsigned long long omega;
+        acc = exact_score<D>(rows, D, P.r, alpha, mode, &omega);
+        if (acc) apply_pair(P, j, rows, D, omega);
+    }
     const unsigned bal = __ballot_sync(0xffffffffu, acc);
     if ((threadIdx.x & 31) == 0 && bal)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->accepted),
-                  (unsigned long long)__popc(bal));
+        atomicAdd(&P.ctrl->acc[P.ctrl->iteration & 3], (unsigned long long)__popc(bal));
 }
 
 // ---- residual + ||r||_0 ---------------------------------------------------
-
-// r_i = y_i - (sum of nonzero x_hat_j, j in N(i), ascending), for one row.
-__device__ __forceinline__ double row_residual(const ProblemDev &P, int i) {
-    const int cnt = P.slot_cnt[i];
-    double s = 0.0;
-    if (cnt <= kSlots) {
-        // The row's contributors are the columns in its slots (every column
-        // with x_hat_j != 0 entered them when it first became nonzero); visit
-        // them in ascending j by repeated minimum selection.
-        const int32_t *sl = P.slots + (size_t)i * kSlots;
-        int js[kSlots];
-#pragma unroll
-        for (int q = 0; q < kSlots; ++q) js[q] = (q < cnt) ? sl[q] : 0x7fffffff;
-        int last = -1;
-        for (int step = 0; step < cnt; ++step) {
-            int nxt = 0x7fffffff;
-#pragma unroll
-            for (int q = 0; q < kSlots; ++q) nxt = (js[q] > last && js[q] < nxt) ? js[q] : nxt;
-            last = nxt;
-            const double v = P.x_hat[nxt];
-            if (v != 0.0) s = __dadd_rn(s, v);
-        }
-    } else {
-        // More contributors than slots: walk the whole CSR row.
-        for (int64_t p = P.csr_ptr[i]; p < P.csr_ptr[i + 1]; ++p) {
-            const double v = P.x_hat[P.csr_cols[p]];
-            if (v != 0.0) s = __dadd_rn(s, v);
-        }
-    }
-    return __dsub_rn(P.y[i], s);
-}
 
 __global__ void __launch_bounds__(256) k_residual(ProblemDev P) {
     if (ld_volatile(&P.ctrl->status) != kRunning) return;
@@ -153,11 +83,11 @@ __global__ void __launch_bounds__(256) k_residual(ProblemDev P) {
         const double ro = P.r[i];
         delta = (long long)(rn != 0.0) - (long long)(ro != 0.0);
         P.r[i] = rn;
+        P.fp[i] = fingerprint(rn);
     }
     delta = warp_sum_ll(delta);
     if ((threadIdx.x & 31) == 0 && delta)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0_delta),
-                  (unsigned long long)delta);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0), (unsigned long long)delta);
 }
 
 // ---- stop rule --------------------------------------------------------------
@@ -165,14 +95,13 @@ __global__ void __launch_bounds__(256) k_residual(ProblemDev P) {
 __global__ void k_finish(ProblemDev P) {
     DecodeCtrl *c = P.ctrl;
     if (c->status != kRunning) return;
-    if (c->accepted == 0) {
+    const int slot = c->iteration & 3;
+    if (c->acc[slot] == 0) {
         c->status = CCS_STALLED;
         return;
     }
+    c->acc[slot] = 0;
     c->iteration += 1;
-    c->r0 += c->r0_delta;
-    c->accepted = 0;
-    c->r0_delta = 0;
     if (P.r0_hist) P.r0_hist[c->iteration] = c->r0;
     if (c->r0 == 0) c->status = CCS_CONVERGED;
     else if (c->iteration >= c->max_iter) c->status = CCS_MAX_ITER;
@@ -217,11 +146,12 @@ int check_params(const ccs_params *p, int d) {
         set_last_error("unknown score_mode %d", p->score_mode);
         return CCS_EINVAL;
     }
-    if (p->engine < CCS_ENGINE_AUTO || p->engine > CCS_ENGINE_PERSISTENT) {
+    if (p->engine != CCS_ENGINE_AUTO && p->engine != CCS_ENGINE_HOST_LOOP &&
+        p->engine != CCS_ENGINE_PERSISTENT) {
         set_last_error("unknown engine %d", p->engine);
         return CCS_EINVAL;
     }
-    if (p->watchdog_ms < 0 || p->reserved[0] || p->reserved[1] || p->reserved[2]) {
+    if (p->watchdog_ms < 0 || p->reserved[0] || p->reserved[1]) {
         set_last_error("bad watchdog_ms or nonzero reserved fields");
         return CCS_EINVAL;
     }
@@ -230,8 +160,8 @@ int check_params(const ccs_params *p, int d) {
 
 // Host-driven loop: one score, residual and stop-rule launch per iteration,
 // then a 64-byte read of the control block to decide whether to go on.
-static int decode_host_loop(const ProblemDev &P, const ccs_params &p, ccs_result *out,
-                            cudaStream_t s) {
+int decode_host_loop(const ProblemDev &P, const ccs_params &p, ccs_result *out,
+                     cudaStream_t s) {
     score_fn score = score_kernel(P.d);
     const int nb_cols = (P.n + 255) / 256, nb_rows = (P.m + 255) / 256;
     const long long big = P.n > P.m ? P.n : P.m;
@@ -290,7 +220,7 @@ extern "C" int ccs_decode_parallel_l0(int32_t n, int32_t m, int32_t d, const int
         set_last_error("ccs_decode_parallel_l0: null pointer argument");
         return CCS_EINVAL;
     }
-    const size_t need = decode_ws_layout(n, m, nullptr, nullptr);
+    const size_t need = decode_ws_layout(n, m, nullptr, nullptr) + engine_ws_bytes(1);
     if (ws_bytes < need) {
         set_last_error("ccs_decode_parallel_l0: workspace %zu < %zu bytes", ws_bytes, need);
         return CCS_ENOMEM;
@@ -306,7 +236,9 @@ extern "C" int ccs_decode_parallel_l0(int32_t n, int32_t m, int32_t d, const int
     P.x_hat = x_hat;
     P.r = r;
     P.r0_hist = r0_hist;
-    decode_ws_layout(n, m, &P, static_cast<char *>(ws));
+    const size_t own = decode_ws_layout(n, m, &P, static_cast<char *>(ws));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    return decode_host_loop(P, p, out, s);
+    if (p.engine == CCS_ENGINE_HOST_LOOP) return decode_host_loop(P, p, out, s);
+    std::vector<ProblemDev> one(1, P);
+    return engine_run(one, p, out, static_cast<char *>(ws) + own, s);
 }

@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <vector>
 
 #include "ccs.h"
 
@@ -20,14 +21,14 @@ enum ErrorBits : int {
 
 // Per-problem decode state kept in the workspace (device memory).
 struct alignas(64) DecodeCtrl {
-    long long r0;         // ||r||_0 after the last completed iteration
-    long long accepted;   // accepted pairs in the current iteration
-    long long r0_delta;   // change of ||r||_0 made by the current residual phase
-    int iteration;        // completed iterations
-    int status;           // kRunning or CCS_CONVERGED / _STALLED / _MAX_ITER
-    int error;            // ErrorBits
+    unsigned long long acc[4];  // accepted pairs, ring indexed by iteration & 3
+    long long r0;               // ||r||_0 of the current r (residual phases add
+                                // their exact integer change)
+    int iteration;              // completed iterations
+    int status;                 // kRunning or CCS_CONVERGED / _STALLED / _MAX_ITER
+    int error;                  // ErrorBits
     int max_iter;
-    int pad[6];
+    long long pad;
 };
 static_assert(sizeof(DecodeCtrl) == 64, "DecodeCtrl layout");
 
@@ -46,6 +47,7 @@ struct ProblemDev {
     uint8_t *in_slots;    // n: column already entered in its rows' slots
     int32_t *slot_cnt;    // m: columns entered in the row's slots
     int32_t *slots;       // m * kSlots: those columns, unordered
+    uint8_t *fp;          // m: 8-bit fingerprint of r_i (0 iff r_i == 0)
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -63,7 +65,9 @@ __host__ inline size_t decode_ws_layout(int n, int m, ProblemDev *pd, char *base
     char *in_slots = take((size_t)n);
     char *slot_cnt = take((size_t)m * 4);
     char *slots = take((size_t)m * kSlots * 4);
+    char *fp = take((size_t)m + 16);
     if (pd) {
+        pd->fp = reinterpret_cast<uint8_t *>(fp);
         pd->ctrl = reinterpret_cast<DecodeCtrl *>(ctrl);
         pd->touched = reinterpret_cast<uint8_t *>(touched);
         pd->in_slots = reinterpret_cast<uint8_t *>(in_slots);
@@ -116,6 +120,15 @@ bool profiling();
 int prof_start(int kind, cudaStream_t s);
 void prof_stop(int slot, cudaStream_t s);
 void prof_collect();
+void prof_add(int kind, double ms);
+
+// host-driven loop (ccs_decode.cu)
+int decode_host_loop(const ProblemDev &P, const ccs_params &p, ccs_result *out, cudaStream_t s);
+
+// persistent engine (ccs_engine.cu)
+size_t engine_ws_bytes(int P);
+int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *out, char *eng,
+               cudaStream_t s);
 int check_params(const ccs_params *p, int d);
 
 }  // namespace ccs

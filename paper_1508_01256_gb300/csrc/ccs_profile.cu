@@ -68,6 +68,13 @@ void prof_collect() {
     g_pending.clear();
 }
 
+void prof_add(int kind, double ms) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_on) return;
+    g_times[kind].launches += 1;
+    g_times[kind].total_ms += ms;
+}
+
 }  // namespace ccs
 
 using namespace ccs;

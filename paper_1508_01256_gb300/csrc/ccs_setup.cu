@@ -313,13 +313,14 @@ void ccs_params_init(ccs_params *p) {
     p->score_mode = CCS_SCORE_L0_DECREASE;
     p->engine = CCS_ENGINE_AUTO;
     p->watchdog_ms = 0;
-    p->reserved[0] = p->reserved[1] = p->reserved[2] = 0;
+    p->debug_flags = 0;
+    p->reserved[0] = p->reserved[1] = 0;
 }
 
 size_t ccs_workspace_size(int32_t op, int32_t n, int32_t m, int32_t d) {
     if (check_sizes(n, m, d) != CCS_OK) return 0;
     if (op == CCS_OP_MAKE_EXPANDER) return make_expander_ws(n, m);
-    if (op == CCS_OP_DECODE) return decode_ws_layout(n, m, nullptr, nullptr);
+    if (op == CCS_OP_DECODE) return decode_ws_layout(n, m, nullptr, nullptr) + engine_ws_bytes(1);
     return 0;
 }
 

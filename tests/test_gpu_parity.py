@@ -265,3 +265,57 @@ def test_iterations_within_log_k(ccs):
         g = ccs.decode_parallel_l0(csc, ptr, cols, y)
         assert g.status == ccs.CONVERGED
         assert g.iterations <= math.log(k) + 2
+
+
+# ---- engines -------------------------------------------------------------------
+
+@pytest.mark.parametrize("engine", [1, 3])
+@pytest.mark.parametrize("shape", [(4096, 410, 7, 41), (2 ** 20, 2 ** 17, 7, 26214),
+                                   (300000, 300, 9, 30), (5000, 250000, 5, 2000),
+                                   (60001, 6000, 16, 900)])
+def test_engines_match_oracle(ccs, orc, engine, shape):
+    """Host-driven loop and persistent engine, each bit-identical to the
+    oracle; the last two shapes take the no-fingerprint path (m too large
+    for shared memory) and the 512-thread d=16 engine."""
+    n, m, d, k = shape
+    p = inputs.make_problem(n, m, d, k, 4000 + n % 97)
+    g, ref = _decode_both(ccs, orc, p, engine=engine)
+    assert_same_decode(g, ref)
+
+
+def test_watchdog_times_out_and_context_survives(ccs, orc):
+    """Test hook: CTA 0 never arrives at the first score barrier, so every
+    CTA's bounded wait runs out (200 ms); the call reports CCS_ETIMEOUT and
+    the next decode on the same context is correct."""
+    p = inputs.plain_small(seed=12)
+    csc, ptr, cols, y = device_problem(ccs, p)
+    with pytest.raises(ccs.CcsError) as ei:
+        ccs.decode_parallel_l0(csc, ptr, cols, y, engine=ccs.ENGINE_PERSISTENT,
+                               watchdog_ms=200, debug_flags=1)
+    assert ei.value.code == ccs.CCS_ETIMEOUT
+    g = ccs.decode_parallel_l0(csc, ptr, cols, y, engine=ccs.ENGINE_PERSISTENT)
+    A, y_ref = oracle_problem(orc, p)
+    assert_same_decode(g, orc.parallel_l0(A, p.m, y_ref))
+
+
+@pytest.mark.parametrize("engine", [1, 3])
+def test_mixed_batch_matches_oracle(ccs, orc, engine):
+    """A mixed batch (n log-uniform in [2^12, 2^16], delta, rho, d drawn as in
+    the batched workload) in one call equals the oracle problem by problem."""
+    probs = inputs.batch_problems(40, seed=77, log2n_hi=16.0)
+    items = [device_problem(ccs, p) for p in probs]
+    outs = ccs.decode_batch(items, history=True, engine=engine)
+    for p, g in zip(probs, outs):
+        A, y_ref = oracle_problem(orc, p)
+        assert_same_decode(g, orc.parallel_l0(A, p.m, y_ref))
+
+
+def test_batch_order_does_not_matter(ccs):
+    probs = inputs.batch_problems(12, seed=5, log2n_hi=15.0)
+    items = [device_problem(ccs, p) for p in probs]
+    fwd = ccs.decode_batch(items)
+    rev = ccs.decode_batch(items[::-1])[::-1]
+    for a, b in zip(fwd, rev):
+        assert a.status == b.status and a.iterations == b.iterations
+        assert np.array_equal(a.x_hat.cpu().numpy(), b.x_hat.cpu().numpy())
+        assert np.array_equal(a.r.cpu().numpy(), b.r.cpu().numpy())
