@@ -235,6 +235,11 @@ enum {
                               under CCS_K_SCORE / CCS_K_RESIDUAL (device
                               timer between grid barriers, one entry per
                               iteration)                                    */
+    CCS_K_PHASE_FP = 5,     /* score phase seen from CTA 0: wait for the
+                              residual fingerprints                         */
+    CCS_K_PHASE_STREAM = 6, /* ... stream of the CSC through the fingerprint
+                              filter                                        */
+    CCS_K_PHASE_QUEUE = 7,  /* ... exact scoring of the queued candidates    */
     CCS_K_COUNT = 8
 };
 typedef struct {
@@ -245,6 +250,12 @@ typedef struct {
 CCS_API int ccs_profile_begin(void);
 /* times: array of CCS_K_COUNT entries (host). */
 CCS_API int ccs_profile_end(ccs_kernel_time *times);
+/* Phase times of one iteration of the last persistent launch made while
+ * profiling (device timer between grid barriers): phase_us[0] score phase,
+ * [1] residual phase, [2..4] CTA 0's score sub-phases (fingerprints in,
+ * stream, queued candidates; -1 when not recorded).  CCS_EINVAL if that
+ * iteration was not recorded. */
+CCS_API int ccs_profile_phases(int32_t iteration, double *phase_us);
 /* Number of kernels this library has launched since it was loaded. */
 CCS_API int64_t ccs_launch_count(void);
 

@@ -64,7 +64,8 @@ _lib = None
 
 K_INIT, K_SCORE, K_RESIDUAL, K_FINISH, K_PERSISTENT, K_COUNT = 0, 1, 2, 3, 4, 8
 KERNEL_NAMES = {K_INIT: "init", K_SCORE: "score", K_RESIDUAL: "residual",
-                K_FINISH: "finish", K_PERSISTENT: "persistent"}
+                K_FINISH: "finish", K_PERSISTENT: "persistent", 5: "score.fingerprints",
+                6: "score.stream", 7: "score.queue"}
 
 
 class KernelTime(ctypes.Structure):
@@ -103,6 +104,8 @@ def lib() -> ctypes.CDLL:
                                        ctypes.POINTER(Result), P, sz, P]
         l.ccs_profile_begin.argtypes = []
         l.ccs_profile_end.argtypes = [ctypes.POINTER(KernelTime)]
+        l.ccs_profile_phases.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
+        l.ccs_profile_phases.restype = ctypes.c_int
         l.ccs_launch_count.argtypes = []
         l.ccs_launch_count.restype = ctypes.c_int64
         for name in ("ccs_make_expander", "ccs_measure", "ccs_decode_parallel_l0",
@@ -206,6 +209,15 @@ def ccs_profile_end() -> dict:
     _check(lib().ccs_profile_end(arr), "ccs_profile_end")
     return {KERNEL_NAMES.get(k, str(k)): (int(arr[k].launches), float(arr[k].total_ms))
             for k in range(K_COUNT) if arr[k].launches}
+
+
+def ccs_profile_phases(iteration: int):
+    """(score_us, residual_us, fp_us, stream_us, queue_us) of one iteration of
+    the last profiled persistent launch, or None."""
+    arr = (ctypes.c_double * 5)()
+    if lib().ccs_profile_phases(iteration, arr) != CCS_OK:
+        return None
+    return tuple(arr)
 
 
 def ccs_launch_count() -> int:

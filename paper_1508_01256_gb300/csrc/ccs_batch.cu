@@ -11,7 +11,7 @@ static size_t batch_ws(const ccs_problem *probs, int32_t count) {
         if (check_sizes(probs[q].n, probs[q].m, probs[q].d) != CCS_OK) return 0;
         total += decode_ws_layout(probs[q].n, probs[q].m, nullptr, nullptr);
     }
-    return total + engine_ws_bytes(count);
+    return engine_header_bytes(count) + total;
 }
 
 }  // namespace ccs
@@ -51,7 +51,8 @@ extern "C" int ccs_decode_batch(const ccs_problem *probs, int32_t count, const c
         return CCS_ENOMEM;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    char *base = static_cast<char *>(ws);
+    char *hdr = static_cast<char *>(ws);
+    char *base = hdr + engine_header_bytes(count);
     std::vector<ProblemDev> pds(count);
     for (int32_t q = 0; q < count; ++q) {
         const ccs_problem &pr = probs[q];
@@ -67,6 +68,7 @@ extern "C" int ccs_decode_batch(const ccs_problem *probs, int32_t count, const c
         P.x_hat = pr.x_hat;
         P.r = pr.r;
         P.r0_hist = pr.r0_hist;
+        P.ctrl = header_ctrl(hdr, q);
         base += decode_ws_layout(pr.n, pr.m, &P, base);
     }
     if (p.engine == CCS_ENGINE_HOST_LOOP) {
@@ -77,5 +79,5 @@ extern "C" int ccs_decode_batch(const ccs_problem *probs, int32_t count, const c
         }
         return CCS_OK;
     }
-    return engine_run(pds, p, out, base, s);
+    return engine_run(pds, p, out, hdr, s);
 }

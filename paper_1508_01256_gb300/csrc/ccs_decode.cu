@@ -35,7 +35,7 @@ __global__ void k_init(ProblemDev P) {
         P.r[i] = v;
         P.fp[i] = fingerprint(v);
         P.touched[i] = 0;
-        P.slot_cnt[i] = 0;
+        P.slots[(size_t)i * kSlotRec] = 0;
         nz += (v != 0.0);
     }
     nz = warp_sum_ll(nz);
@@ -64,11 +64,17 @@ __global__ void __launch_bounds__(256) k_score(ProblemDev P, int alpha, int mode
         for (int t = 0; t < D; ++t) rows[t] = __ldg(P.csc_rows + (size_t)j * D + t);
         unsigned long long omega;
         acc = exact_score<D>(rows, D, P.r, alpha, mode, &omega);
-        if (acc) apply_pair(P, j, rows, D, omega);
+        if (acc) apply_pair<D>(P, j, rows, D, omega);
     }
+    // block total on chip, then one global atomic per block
+    __shared__ unsigned s_acc;
+    if (threadIdx.x == 0) s_acc = 0;
+    __syncthreads();
     const unsigned bal = __ballot_sync(0xffffffffu, acc);
-    if ((threadIdx.x & 31) == 0 && bal)
-        atomicAdd(&P.ctrl->acc[P.ctrl->iteration & 3], (unsigned long long)__popc(bal));
+    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(&s_acc, (unsigned)__popc(bal));
+    __syncthreads();
+    if (threadIdx.x == 0 && s_acc)
+        atomicAdd(&P.ctrl->acc[P.ctrl->iteration & 3], (unsigned long long)s_acc);
 }
 
 // ---- residual + ||r||_0 ---------------------------------------------------
@@ -85,9 +91,15 @@ __global__ void __launch_bounds__(256) k_residual(ProblemDev P) {
         P.r[i] = rn;
         P.fp[i] = fingerprint(rn);
     }
+    __shared__ long long s_delta;
+    if (threadIdx.x == 0) s_delta = 0;
+    __syncthreads();
     delta = warp_sum_ll(delta);
     if ((threadIdx.x & 31) == 0 && delta)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0), (unsigned long long)delta);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&s_delta), (unsigned long long)delta);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_delta)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0), (unsigned long long)s_delta);
 }
 
 // ---- stop rule --------------------------------------------------------------
@@ -220,7 +232,7 @@ extern "C" int ccs_decode_parallel_l0(int32_t n, int32_t m, int32_t d, const int
         set_last_error("ccs_decode_parallel_l0: null pointer argument");
         return CCS_EINVAL;
     }
-    const size_t need = decode_ws_layout(n, m, nullptr, nullptr) + engine_ws_bytes(1);
+    const size_t need = engine_header_bytes(1) + decode_ws_layout(n, m, nullptr, nullptr);
     if (ws_bytes < need) {
         set_last_error("ccs_decode_parallel_l0: workspace %zu < %zu bytes", ws_bytes, need);
         return CCS_ENOMEM;
@@ -236,9 +248,11 @@ extern "C" int ccs_decode_parallel_l0(int32_t n, int32_t m, int32_t d, const int
     P.x_hat = x_hat;
     P.r = r;
     P.r0_hist = r0_hist;
-    const size_t own = decode_ws_layout(n, m, &P, static_cast<char *>(ws));
+    char *base = static_cast<char *>(ws);
+    P.ctrl = header_ctrl(base, 0);
+    decode_ws_layout(n, m, &P, base + engine_header_bytes(1));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (p.engine == CCS_ENGINE_HOST_LOOP) return decode_host_loop(P, p, out, s);
     std::vector<ProblemDev> one(1, P);
-    return engine_run(one, p, out, static_cast<char *>(ws) + own, s);
+    return engine_run(one, p, out, base, s);
 }

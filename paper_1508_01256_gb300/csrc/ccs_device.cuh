@@ -2,8 +2,8 @@
 // host-driven kernels (ccs_decode.cu) and the persistent engine
 // (ccs_engine.cu).
 //
-// Data read across phases of one persistent launch (r, x_hat, fp, slots,
-// slot_cnt, touched, in_slots) is loaded with ld.global.cg (L2, never a
+// Data read across phases of one persistent launch (r, x_hat, fp, slot
+// records, touched, in_slots) is loaded with ld.global.cg (L2, never a
 // stale L1 line); the matrix and y are read-only and go through the
 // read-only path.
 #pragma once
@@ -21,6 +21,63 @@ __device__ __forceinline__ uint8_t fingerprint(double v) {
     unsigned long long h = (b ^ (b >> 31)) * 0x9e3779b97f4a7c15ull;
     const unsigned f = (unsigned)(h >> 56);
     return (uint8_t)(f == 0u ? 1u : f);
+}
+
+// Largest multiplicity of a nonzero byte among the first d bytes of the
+// packed words w0..w3 (4 bytes each, position t in byte t%4 of word t/4),
+// counting each of the d(d-1)/2 pairs once.  Out of line, arguments in
+// registers: most columns never need it.
+template <int DMAX>
+__device__ __noinline__ int fingerprint_max_count(unsigned w0, unsigned w1, unsigned w2,
+                                                  unsigned w3, int d) {
+    const unsigned w[4] = {w0, w1, w2, w3};
+    unsigned f[DMAX];
+    int cnt[DMAX];
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t) {
+        f[t] = (w[t >> 2] >> (8 * (t & 3))) & 0xffu;
+        cnt[t] = 1;
+    }
+#pragma unroll
+    for (int a = 0; a < DMAX; ++a)
+#pragma unroll
+        for (int b = a + 1; b < DMAX; ++b) {
+            const int e = (b < d) & (f[a] == f[b]);
+            cnt[a] += e;
+            cnt[b] += e;
+        }
+    int F = 0;
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t) F = (t < d && f[t] != 0u && cnt[t] > F) ? cnt[t] : F;
+    return F;
+}
+
+// Exact score from the d gathered values v (value_bits form) -- the
+// computation of exact_score without its loads.
+template <int DMAX>
+__device__ __forceinline__ bool exact_score_values(const unsigned long long (&v)[DMAX], int d,
+                                                   int alpha, int mode,
+                                                   unsigned long long *omega) {
+    int c0 = 0;
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t) c0 += (t < d) & (v[t] == 0ull);
+    int best_cnt = 0;
+    unsigned long long best_bits = 0ull, best_key = ~0ull;
+#pragma unroll
+    for (int a = 0; a < DMAX; ++a) {
+        int c = 0;
+#pragma unroll
+        for (int b = 0; b < DMAX; ++b) c += (b < d) & (v[b] == v[a]);
+        const unsigned long long key = order_key(v[a]);
+        const bool better = (a < d) && (v[a] != 0ull) &&
+                            (c > best_cnt || (c == best_cnt && key < best_key));
+        best_cnt = better ? c : best_cnt;
+        best_key = better ? key : best_key;
+        best_bits = better ? v[a] : best_bits;
+    }
+    const int score = (mode == CCS_SCORE_COUNT) ? best_cnt : best_cnt - c0;
+    *omega = best_bits;
+    return best_cnt > 0 && score >= alpha;
 }
 
 // Exact score of one column from its d row indices `rows` (stride 1).
@@ -61,77 +118,131 @@ __device__ __forceinline__ bool exact_score(const int32_t *rows, int d, const do
 // nonzero fingerprint among the d rows and c0 the number of zero rows,
 // every value omega has c_omega <= F, so score <= F - c0 (Eq. (15)) or
 // <= F (Alg. 8).  Returns false when no pair of this column can reach alpha.
+// The cheap test (F <= number of nonzero rows) runs first; the pair counts
+// only for the columns that pass it.
 template <int DMAX>
 __device__ __forceinline__ bool may_accept(const uint8_t *fp_smem, const int32_t *rows, int d,
                                            int alpha, int mode) {
-    unsigned f[DMAX];
-#pragma unroll
-    for (int t = 0; t < DMAX; ++t) f[t] = (t < d) ? (unsigned)fp_smem[rows[t]] : 0u;
+    unsigned w[4] = {0u, 0u, 0u, 0u};
     int c0 = 0;
 #pragma unroll
-    for (int t = 0; t < DMAX; ++t) c0 += (t < d) & (f[t] == 0u);
-    // quick bound: F <= number of nonzero rows
-    const int nz = d - c0;
-    if (((mode == CCS_SCORE_COUNT) ? nz : nz - c0) < alpha) return false;
-    int F = 0;
-#pragma unroll
-    for (int a = 0; a < DMAX; ++a) {
-        int c = 0;
-#pragma unroll
-        for (int b = 0; b < DMAX; ++b) c += (b < d) & (f[b] == f[a]);
-        F = (a < d && f[a] != 0u && c > F) ? c : F;
+    for (int t = 0; t < DMAX; ++t) {
+        const unsigned f = (t < d) ? (unsigned)fp_smem[rows[t]] : 0u;
+        c0 += (t < d) & (f == 0u);
+        w[t >> 2] |= f << (8 * (t & 3));
     }
-    return ((mode == CCS_SCORE_COUNT) ? F : F - c0) >= alpha;
+    const int need = (mode == CCS_SCORE_COUNT) ? alpha : alpha + c0;  // F must reach this
+    if (d - c0 < need) return false;
+    return fingerprint_max_count<DMAX>(w[0], w[1], w[2], w[3], d) >= need;
+}
+
+// Enter column j in the slot records of its d rows: all d slot claims
+// (atomicAdd on each record's count) are issued before any column index is
+// stored, so the claims travel together instead of one round trip each.
+template <int DMAX>
+__device__ __forceinline__ void enter_slots(const ProblemDev &P, int j, const int32_t *rows, int d) {
+    int pos[DMAX];
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t)
+        pos[t] = (t < d) ? atomicAdd(P.slots + (size_t)rows[t] * kSlotRec, 1) : kSlots;
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t)
+        if (pos[t] < kSlots) P.slots[(size_t)rows[t] * kSlotRec + 1 + pos[t]] = j;
 }
 
 // Apply an accepted pair (Alg. 2: x_hat_j <- x_hat_j + omega_j), mark the
 // column's rows for the residual phase and, the first time the column turns
 // nonzero, enter it in its rows' contributor slots.
+template <int DMAX>
 __device__ __forceinline__ void apply_pair(const ProblemDev &P, int j, const int32_t *rows, int d,
                                            unsigned long long omega_bits) {
     const double omega = __longlong_as_double((long long)omega_bits);
     P.x_hat[j] = __dadd_rn(__ldcg(P.x_hat + j), omega);
-    for (int t = 0; t < d; ++t) P.touched[rows[t]] = 1;
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t)
+        if (t < d) P.touched[rows[t]] = 1;
     if (!__ldcg(P.in_slots + j)) {
         P.in_slots[j] = 1;
-        for (int t = 0; t < d; ++t) {
-            const int pos = atomicAdd(&P.slot_cnt[rows[t]], 1);
-            if (pos < kSlots) P.slots[(size_t)rows[t] * kSlots + pos] = j;
+        enter_slots<DMAX>(P, j, rows, d);
+    }
+}
+
+// apply_pair with x_hat_j and the in-slots flag already loaded (issued in the
+// same round trip as the column's r gathers).
+template <int DMAX>
+__device__ __forceinline__ void apply_pair_loaded(const ProblemDev &P, int j, const int32_t *rows,
+                                                  int d, unsigned long long omega_bits,
+                                                  double xj, uint8_t in_slots) {
+    P.x_hat[j] = __dadd_rn(xj, __longlong_as_double((long long)omega_bits));
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t)
+        if (t < d) P.touched[rows[t]] = 1;
+    if (!in_slots) {
+        P.in_slots[j] = 1;
+        enter_slots<DMAX>(P, j, rows, d);
+    }
+}
+
+// Ordered row sum from the row's 64-byte slot record js[0..kSlotRec)
+// (count, then the columns): the sum of the nonzero x_hat_j, j in N(i), in
+// ascending j, from +0.0.
+__device__ __forceinline__ double row_sum_from_record(const ProblemDev &P, int i,
+                                                      int (&js)[kSlotRec]) {
+    const int cnt = js[0];
+    double s = 0.0;
+    if (cnt <= kSlots) {
+        // The row's contributors are the columns in its record (every column
+        // with x_hat_j != 0 entered it when it first became nonzero).  Fetch
+        // all their x_hat_j at once, then add them in ascending j by repeated
+        // minimum selection.
+        double v[kSlots];
+#pragma unroll
+        for (int q = 0; q < kSlots; ++q) {
+            js[1 + q] = (q < cnt) ? js[1 + q] : 0x7fffffff;
+            v[q] = (q < cnt) ? __ldcg(P.x_hat + js[1 + q]) : 0.0;
         }
+        int last = -1;
+        for (int step = 0; step < cnt; ++step) {
+            int nxt = 0x7fffffff;
+            double vn = 0.0;
+#pragma unroll
+            for (int q = 0; q < kSlots; ++q) {
+                const bool take = js[1 + q] > last && js[1 + q] < nxt;
+                nxt = take ? js[1 + q] : nxt;
+                vn = take ? v[q] : vn;
+            }
+            last = nxt;
+            if (vn != 0.0) s = __dadd_rn(s, vn);
+        }
+    } else {
+        // More contributors than slots: walk the whole CSR row.
+        const int64_t e = __ldg(P.csr_ptr + i + 1);
+        for (int64_t p = __ldg(P.csr_ptr + i); p < e; ++p) {
+            const double xv = __ldcg(P.x_hat + __ldg(P.csr_cols + p));
+            if (xv != 0.0) s = __dadd_rn(s, xv);
+        }
+    }
+    return s;
+}
+
+__device__ __forceinline__ void load_record(const ProblemDev &P, int i, int (&js)[kSlotRec]) {
+    const int4 *rec4 = reinterpret_cast<const int4 *>(P.slots + (size_t)i * kSlotRec);
+#pragma unroll
+    for (int q = 0; q < kSlotRec / 4; ++q) {
+        const int4 v = __ldcg(rec4 + q);
+        js[4 * q] = v.x;
+        js[4 * q + 1] = v.y;
+        js[4 * q + 2] = v.z;
+        js[4 * q + 3] = v.w;
     }
 }
 
 // r_i = y_i - (sum of the nonzero x_hat_j, j in N(i), in ascending j, from
 // +0.0), the residual step of Alg. 2 for one row.
 __device__ __forceinline__ double row_residual(const ProblemDev &P, int i) {
-    const int cnt = __ldcg(P.slot_cnt + i);
-    double s = 0.0;
-    if (cnt <= kSlots) {
-        // The row's contributors are the columns in its slots (every column
-        // with x_hat_j != 0 entered them when it first became nonzero); visit
-        // them in ascending j by repeated minimum selection.
-        const int32_t *sl = P.slots + (size_t)i * kSlots;
-        int js[kSlots];
-#pragma unroll
-        for (int q = 0; q < kSlots; ++q) js[q] = (q < cnt) ? __ldcg(sl + q) : 0x7fffffff;
-        int last = -1;
-        for (int step = 0; step < cnt; ++step) {
-            int nxt = 0x7fffffff;
-#pragma unroll
-            for (int q = 0; q < kSlots; ++q) nxt = (js[q] > last && js[q] < nxt) ? js[q] : nxt;
-            last = nxt;
-            const double v = __ldcg(P.x_hat + nxt);
-            if (v != 0.0) s = __dadd_rn(s, v);
-        }
-    } else {
-        // More contributors than slots: walk the whole CSR row.
-        const int64_t e = __ldg(P.csr_ptr + i + 1);
-        for (int64_t p = __ldg(P.csr_ptr + i); p < e; ++p) {
-            const double v = __ldcg(P.x_hat + __ldg(P.csr_cols + p));
-            if (v != 0.0) s = __dadd_rn(s, v);
-        }
-    }
-    return __dsub_rn(__ldg(P.y + i), s);
+    int js[kSlotRec];
+    load_record(P, i, js);
+    return __dsub_rn(__ldg(P.y + i), row_sum_from_record(P, i, js));
 }
 
 }  // namespace ccs

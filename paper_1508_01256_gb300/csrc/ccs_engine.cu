@@ -6,24 +6,33 @@
 //
 //   init      x_hat <- 0, r <- y, fingerprints of r, ||y||_0
 //   score     every column of every running problem: exact score (Eq. (15)
-//             or Alg. 8) and, if accepted, x_hat_j += omega_j (apply).  The
-//             problem's 8-bit residual fingerprints sit in shared memory when
-//             they fit, so most columns are rejected from on-chip data alone
-//             (a fingerprint count bounds every value's count); only the
-//             columns that may reach alpha gather their d binary64 values.
+//             or Alg. 8) and, if accepted, x_hat_j += omega_j (apply).
 //   residual  every touched row: r_i = y_i - ordered sum of its nonzero
 //             x_hat_j, new fingerprint, exact change of ||r||_0
 //   stop      every CTA applies the stop rule to every problem from the same
 //             counters, so all CTAs agree without another barrier
 //
-// Work unit: a tile of 32 columns (score) or 32 rows (residual), one warp.
-// A CTA owns a contiguous range of tiles, so it loads one problem's
-// fingerprints once per phase.  Every barrier wait is bounded by the
-// watchdog: on time-out the CTA records kErrWatchdog and returns, and the
-// host reports CCS_ETIMEOUT.
+// Score phase, per CTA and problem segment (a contiguous range of 32-column
+// tiles):
+//   - the problem's 8-bit residual fingerprints (m bytes) and the segment's
+//     CSC row indices stream into shared memory by TMA bulk copies
+//     (cp.async.bulk, mbarrier completion); the CSC goes through a ring of
+//     stages so the next chunks are in flight while warps work on this one;
+//   - each warp tests its 32 columns against the fingerprint bound (a value's
+//     count never exceeds its fingerprint's count), from shared memory only;
+//   - the few columns that may reach alpha are queued, then scored exactly,
+//     lane-parallel across the CTA: d binary64 gathers of r each.
+// Problems whose fingerprints do not fit shared memory score every column
+// exactly from the same stages.
+//
+// Every wait (grid barrier, mbarrier) is bounded by the watchdog: on time-out
+// the CTA records kErrWatchdog, gives its in-flight copies a bounded time to
+// land, and returns; the host reports CCS_ETIMEOUT.
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "ccs_device.cuh"
@@ -33,7 +42,12 @@ namespace ccs {
 constexpr int kTile = 32;
 constexpr int kMaxBlocks = 1024;
 constexpr int kMaxStampIters = 1024;
+constexpr int kMaxStages = 6;
+constexpr int kQueueCap = 2048;     // most candidate columns queued per CTA and segment
+constexpr int kMinQueue = 256;      // fewest (more go through the inline exact path)
 constexpr int kFlagSkipArrive = 1;  // test hook: CTA 0 never arrives at barrier 1
+constexpr int kFpChunk = 32768;     // bytes per fingerprint bulk copy
+constexpr int kSubBase = 3 * kMaxStampIters + 2;  // CTA-0 score sub-phase stamps start here
 
 struct Segment {
     int prob, lo, hi, pad;  // tiles [lo, hi) of problem `prob`
@@ -45,17 +59,20 @@ struct EngineArgs {
     int P;
     int alpha, mode, max_iter;
     int fp_cap;                 // bytes of the shared fingerprint buffer
-    int stride;                 // ints per column in a warp's index stage (odd)
+    int stages;                 // CSC ring depth
+    int stage_bytes;            // bytes per stage (one tile per warp)
+    int queue_cap;              // candidate entries (column + its d rows)
     const int *score_ptr;       // G+1 offsets into score_segs (batch only)
     const Segment *score_segs;
     const int *res_ptr;
     const Segment *res_segs;
-    unsigned *arrive;           // monotonic barrier counter
-    int *error;                 // ErrorBits for the whole launch
+    EngineSync *sync;
     unsigned long long *stamps; // globaltimer after each barrier (or null)
     long long watchdog_ns;
     int debug_flags;
 };
+
+// ---- device helpers --------------------------------------------------------
 
 __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
@@ -69,6 +86,61 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     return v;
 }
 
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple
+// of 16), completion counted in bytes on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Bounded wait on an mbarrier phase.  On time-out marks the launch failed.
+__device__ __forceinline__ bool mbar_wait(const EngineArgs &a, uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer() - t0 > (unsigned long long)a.watchdog_ns) {
+            atomicOr(&a.sync->error, kErrWatchdog);
+            return false;
+        }
+    }
+    return true;
+}
+
 // Grid barrier number `index` (0-based).  Returns false if the wait ran past
 // the watchdog (or another CTA already gave up).
 __device__ bool grid_barrier(const EngineArgs &a, unsigned index, bool arrive = true) {
@@ -78,18 +150,18 @@ __device__ bool grid_barrier(const EngineArgs &a, unsigned index, bool arrive = 
         int ok = 1;
         if (arrive) {
             __threadfence();
-            atomicAdd(a.arrive, 1u);
+            atomicAdd(&a.sync->arrive, 1u);
         }
         const unsigned target = (index + 1u) * gridDim.x;
         const unsigned long long t0 = globaltimer();
-        while (ld_acquire(a.arrive) < target) {
-            if (*reinterpret_cast<volatile int *>(a.error) != 0 ||
+        while (ld_acquire(&a.sync->arrive) < target) {
+            if (*reinterpret_cast<volatile int *>(&a.sync->error) != 0 ||
                 globaltimer() - t0 > (unsigned long long)a.watchdog_ns) {
-                atomicOr(a.error, kErrWatchdog);
+                atomicOr(&a.sync->error, kErrWatchdog);
                 ok = 0;
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(32);
         }
         __threadfence();
         if (ok && a.stamps && blockIdx.x == 0 && index < 3u * kMaxStampIters + 1u)
@@ -102,72 +174,6 @@ __device__ bool grid_barrier(const EngineArgs &a, unsigned index, bool arrive = 
 
 __device__ __forceinline__ const ProblemDev &problem(const EngineArgs &a, int p) {
     return a.probs ? a.probs[p] : a.single;
-}
-
-// Stage the d row indices of a tile's columns in shared memory (stride
-// `stride` per column, odd, so that lane-strided reads hit distinct banks).
-__device__ __forceinline__ void stage_tile(const ProblemDev &P, int base, int cols, int stride,
-                                           int32_t *stage, int lane) {
-    const int d = P.d;
-    const int32_t *src = P.csc_rows + (size_t)base * d;
-    const int total = cols * d;
-    if (((reinterpret_cast<uintptr_t>(src) & 15u) == 0) && (total & 3) == 0) {
-        const int4 *src4 = reinterpret_cast<const int4 *>(src);
-        for (int q = lane; q < (total >> 2); q += 32) {
-            const int4 v = __ldg(src4 + q);
-            int e = q << 2;
-            int col = e / d, t = e - col * d;
-            const int vals[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                stage[col * stride + t] = vals[u];
-                if (++t == d) {
-                    t = 0;
-                    ++col;
-                }
-            }
-        }
-    } else {
-        for (int e = lane; e < total; e += 32) {
-            const int col = e / d;
-            stage[col * stride + (e - col * d)] = __ldg(src + e);
-        }
-    }
-}
-
-template <int DMAX>
-__device__ __forceinline__ bool score_tile(const EngineArgs &a, const ProblemDev &P, int tile,
-                                           const uint8_t *s_fp, int32_t *stage, int lane) {
-    const int base = tile * kTile;
-    const int cols = min(kTile, P.n - base);
-    stage_tile(P, base, cols, a.stride, stage, lane);
-    __syncwarp();
-    bool acc = false;
-    if (lane < cols) {
-        const int32_t *rows = stage + lane * a.stride;
-        const bool cand = s_fp ? may_accept<DMAX>(s_fp, rows, P.d, a.alpha, a.mode) : true;
-        if (cand) {
-            unsigned long long omega;
-            acc = exact_score<DMAX>(rows, P.d, P.r, a.alpha, a.mode, &omega);
-            if (acc) apply_pair(P, base + lane, rows, P.d, omega);
-        }
-    }
-    __syncwarp();
-    return acc;
-}
-
-__device__ __forceinline__ long long residual_tile(const ProblemDev &P, int tile, int lane) {
-    const int i = tile * kTile + lane;
-    long long delta = 0;
-    if (i < P.m && __ldcg(P.touched + i)) {
-        P.touched[i] = 0;
-        const double rn = row_residual(P, i);
-        const double ro = __ldcg(P.r + i);
-        delta = (long long)(rn != 0.0) - (long long)(ro != 0.0);
-        P.r[i] = rn;
-        P.fp[i] = fingerprint(rn);
-    }
-    return warp_sum_ll(delta);
 }
 
 // This CTA's segments of a phase.  One problem: a contiguous share of its
@@ -186,7 +192,8 @@ __device__ __forceinline__ SegList my_segments(const EngineArgs &a, bool score) 
         L.one.prob = 0;
         L.one.lo = (int)(tiles * blockIdx.x / gridDim.x);
         L.one.hi = (int)(tiles * (blockIdx.x + 1) / gridDim.x);
-        L.segs = nullptr;  // use `one`
+        L.one.pad = 0;
+        L.segs = nullptr;
         L.count = 1;
     } else {
         const int *ptr = score ? a.score_ptr : a.res_ptr;
@@ -197,22 +204,239 @@ __device__ __forceinline__ SegList my_segments(const EngineArgs &a, bool score) 
     return L;
 }
 
+// Shared-memory state of the score phase.
+struct ScoreSmem {
+    uint8_t *fp;       // fingerprints of the current problem
+    char *stage;       // a.stages * a.stage_bytes
+    int32_t *queue;    // candidate columns
+    uint64_t *full;    // per stage: its chunk has landed (TMA transaction count)
+    uint64_t *empty;   // per stage: every consumer warp is done with it
+    uint64_t *fp_bar;  // fingerprint copy
+    int *qn;           // queue length
+    unsigned long long *acc;  // accepted pairs of this CTA in the current segment
+};
+
+// Columns [col0, col1) of chunk `c` of a segment (tiles lo + c*W .. +W).
+__device__ __forceinline__ void chunk_cols(const ProblemDev &P, int lo, int hi, int c, int per,
+                                           long long &col0, long long &col1) {
+    const int t0 = lo + c * per;
+    const int t1 = min(hi, t0 + per);
+    col0 = (long long)t0 * kTile;
+    col1 = min((long long)P.n, (long long)t1 * kTile);
+}
+
+// Issue chunk `c` into ring slot `slot`: the largest 16-byte multiple of its
+// row indices by TMA (the consumer reads any remaining < 4 ints, which only
+// occur at a problem's last column, from global memory).
+__device__ __forceinline__ void issue_chunk(const EngineArgs &a, const ProblemDev &P, int lo,
+                                            int hi, int c, int per, ScoreSmem &S, int slot) {
+    long long col0, col1;
+    chunk_cols(P, lo, hi, c, per, col0, col1);
+    const uint32_t tma = (uint32_t)((col1 - col0) * P.d * 4) & ~15u;
+    uint64_t *bar = &S.full[slot];
+    mbar_expect_tx(bar, tma);
+    if (tma) bulk_g2s(S.stage + (size_t)slot * a.stage_bytes, P.csc_rows + col0 * P.d, tma, bar);
+}
+
+// Score phase of one segment.  Warp 0 is the producer: its lane 0 streams
+// the fingerprints and the CSC chunks by TMA, refilling a stage as soon as
+// every consumer warp has released it.  Warps 1.. consume one 32-column tile
+// of each chunk: the fingerprint bound from shared memory, candidates into
+// the queue.  Then every warp scores the queued candidates exactly.
+template <int DMAX>
+__device__ __forceinline__ void score_segment(const EngineArgs &a, const ProblemDev &P,
+                                              const Segment &sg, int g, ScoreSmem &S,
+                                              unsigned &chunk_seq, unsigned &fp_seq, bool &ok) {
+    const int warps = blockDim.x >> 5;
+    const int per = warps - 1;  // tiles per chunk: one per consumer warp
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int d = P.d;
+    const bool use_fp = P.pad != 0;
+    const int tiles = sg.hi - sg.lo;
+    const int nchunks = (tiles + per - 1) / per;
+    unsigned long long *acc_slot = &P.ctrl->acc[g & 3];
+
+    __syncthreads();  // previous users of the queue and fingerprints are done
+    if (threadIdx.x == 0) {
+        *S.qn = 0;
+        *S.acc = 0;
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+        if (lane == 0 && ok) {
+            if (use_fp) {
+                const uint32_t total = (uint32_t)align_up((size_t)P.m, 16);
+                mbar_expect_tx(S.fp_bar, total);
+                for (uint32_t off = 0; off < total; off += kFpChunk)
+                    bulk_g2s(S.fp + off, P.fp + off, min((uint32_t)kFpChunk, total - off), S.fp_bar);
+            }
+            for (int c = 0; c < nchunks; ++c) {
+                const unsigned seq = chunk_seq + c;
+                const int slot = seq % a.stages;
+                if (!mbar_wait(a, &S.empty[slot], ((seq / a.stages) & 1u) ^ 1u)) {
+                    ok = false;
+                    break;
+                }
+                issue_chunk(a, P, sg.lo, sg.hi, c, per, S, slot);
+            }
+        }
+    } else {
+        if (use_fp) ok = ok && mbar_wait(a, S.fp_bar, fp_seq & 1u);
+        if (a.stamps && blockIdx.x == 0 && threadIdx.x == 32 && g < kMaxStampIters)
+            a.stamps[kSubBase + 3 * g] = globaltimer();
+        for (int c = 0; c < nchunks; ++c) {
+            const unsigned seq = chunk_seq + c;
+            const int slot = seq % a.stages;
+            ok = ok && mbar_wait(a, &S.full[slot], (seq / a.stages) & 1u);
+            const int32_t *stage =
+                reinterpret_cast<const int32_t *>(S.stage + (size_t)slot * a.stage_bytes);
+            long long col0, col1;
+            chunk_cols(P, sg.lo, sg.hi, c, per, col0, col1);
+            const long long e_tma = (((col1 - col0) * d * 4) & ~15ll) / 4;  // ints that came by TMA
+            const int tile = sg.lo + c * per + (warp - 1);
+            bool acc = false;
+            if (ok && tile < sg.hi) {
+                const int base = tile * kTile;
+                const int cols = min(kTile, P.n - base);
+                if (lane < cols) {
+                    const int j = base + lane;
+                    const long long e0 = (long long)(j - col0) * d;  // first int of column j
+                    int32_t rows[DMAX];
+#pragma unroll
+                    for (int t = 0; t < DMAX; ++t)
+                        rows[t] = (t < d) ? ((e0 + t < e_tma) ? stage[e0 + t]
+                                                              : __ldg(P.csc_rows + (size_t)j * d + t))
+                                          : 0;
+                    bool inline_exact = true;
+                    if (use_fp) {
+                        inline_exact = false;
+                        if (may_accept<DMAX>(S.fp, rows, d, a.alpha, a.mode)) {
+                            const int q = atomicAdd(S.qn, 1);
+                            if (q < a.queue_cap) {  // scored after the stream
+                                int32_t *e = S.queue + q * (DMAX + 1);
+                                e[0] = j;
+#pragma unroll
+                                for (int t = 0; t < DMAX; ++t) e[1 + t] = rows[t];
+                            } else {
+                                inline_exact = true;
+                            }
+                        }
+                    }
+                    if (inline_exact) {
+                        unsigned long long omega;
+                        acc = exact_score<DMAX>(rows, d, P.r, a.alpha, a.mode, &omega);
+                        if (acc) apply_pair<DMAX>(P, j, rows, d, omega);
+                    }
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, acc);
+            if (lane == 0 && bal) atomicAdd(S.acc, (unsigned long long)__popc(bal));
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.empty[slot]);  // this warp is done with the stage
+        }
+    }
+    chunk_seq += nchunks;
+    if (use_fp) ++fp_seq;
+    __syncthreads();  // stream done, queue complete
+    if (a.stamps && blockIdx.x == 0 && threadIdx.x == 0 && g < kMaxStampIters)
+        a.stamps[kSubBase + 3 * g + 1] = globaltimer();
+
+    // queued candidates: exact score, lane-parallel over the CTA.  The r
+    // gathers, x_hat_j and the in-slots flag go out in one round trip.
+    const int qn = min(*S.qn, a.queue_cap);
+    for (int b0 = warp * 32; b0 < qn; b0 += blockDim.x) {
+        const int idx = b0 + lane;
+        bool acc = false;
+        if (ok && idx < qn) {
+            const int32_t *e = S.queue + idx * (DMAX + 1);
+            const int j = e[0];
+            int32_t rows[DMAX];
+            unsigned long long v[DMAX];
+#pragma unroll
+            for (int t = 0; t < DMAX; ++t) rows[t] = e[1 + t];
+#pragma unroll
+            for (int t = 0; t < DMAX; ++t) v[t] = (t < d) ? value_bits(__ldcg(P.r + rows[t])) : 0ull;
+            const double xj = __ldcg(P.x_hat + j);
+            const uint8_t ins = __ldcg(P.in_slots + j);
+            unsigned long long omega;
+            acc = exact_score_values<DMAX>(v, d, a.alpha, a.mode, &omega);
+            if (acc) apply_pair_loaded<DMAX>(P, j, rows, d, omega, xj, ins);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, acc);
+        if (lane == 0 && bal) atomicAdd(S.acc, (unsigned long long)__popc(bal));
+    }
+    // one global atomic per CTA and segment (all warps' counts summed on chip)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (*S.acc) atomicAdd(acc_slot, *S.acc);
+        if (a.stamps && blockIdx.x == 0 && g < kMaxStampIters)
+            a.stamps[kSubBase + 3 * g + 2] = globaltimer();
+    }
+}
+
+// One row of the residual phase.  The touched flag, the row's slot record,
+// y_i and the old r_i are independent loads issued together; only touched
+// rows then gather their contributors' x_hat_j.
+__device__ __forceinline__ long long residual_tile(const ProblemDev &P, int tile, int lane) {
+    const int i = tile * kTile + lane;
+    long long delta = 0;
+    if (i < P.m) {
+        const uint8_t touched = __ldcg(P.touched + i);
+        int js[kSlotRec];
+        load_record(P, i, js);
+        const double yi = __ldg(P.y + i);
+        const double ro = __ldcg(P.r + i);
+        if (touched) {
+            P.touched[i] = 0;
+            const double rn = __dsub_rn(yi, row_sum_from_record(P, i, js));
+            delta = (long long)(rn != 0.0) - (long long)(ro != 0.0);
+            P.r[i] = rn;
+            P.fp[i] = fingerprint(rn);
+        }
+    }
+    return warp_sum_ll(delta);
+}
+
 template <int DMAX, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ EngineArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint8_t *s_fp = smem;
-    int32_t *s_stage = reinterpret_cast<int32_t *>(smem + a.fp_cap);
+    extern __shared__ __align__(128) unsigned char smem[];
     constexpr int kWarps = THREADS / 32;
-    int8_t *s_status = reinterpret_cast<int8_t *>(s_stage + kWarps * kTile * a.stride);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int32_t *stage = s_stage + warp * kTile * a.stride;
-    unsigned bar = 0;
+    __shared__ __align__(8) uint64_t s_bars[2 * kMaxStages + 1];
+    __shared__ int s_qn;
+    __shared__ unsigned long long s_acc;
+    __shared__ long long s_sum;
+    ScoreSmem S;
+    S.fp = smem;
+    S.stage = reinterpret_cast<char *>(smem + a.fp_cap);
+    S.queue = reinterpret_cast<int32_t *>(S.stage + (size_t)a.stages * a.stage_bytes);
+    int8_t *s_status = reinterpret_cast<int8_t *>(S.queue + a.queue_cap * (DMAX + 1));
+    S.full = s_bars;
+    S.empty = s_bars + kMaxStages;
+    S.fp_bar = &s_bars[2 * kMaxStages];
+    S.qn = &s_qn;
+    S.acc = &s_acc;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned bar = 0, chunk_seq = 0, fp_seq = 0;
+    bool ok = true;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kMaxStages; ++s) {
+            mbar_init(&S.full[s], 1);            // the producer's expect_tx arrival
+            mbar_init(&S.empty[s], kWarps - 1);  // one arrival per consumer warp
+        }
+        mbar_init(S.fp_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
 
     // ---- init: x_hat <- 0, r <- y (Alg. 2, first line) --------------------
     const long long gtid = blockIdx.x * (long long)THREADS + threadIdx.x;
     const long long gstride = (long long)gridDim.x * THREADS;
     for (int p = 0; p < a.P; ++p) {
         const ProblemDev &P = problem(a, p);
+        if (threadIdx.x == 0) s_sum = 0;
+        __syncthreads();
         for (long long j = gtid; j < P.n; j += gstride) {
             P.x_hat[j] = 0.0;
             P.in_slots[j] = 0;
@@ -223,12 +447,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
             P.r[i] = v;
             P.fp[i] = fingerprint(v);
             P.touched[i] = 0;
-            P.slot_cnt[i] = 0;
+            P.slots[(size_t)i * kSlotRec] = 0;
             nz += (v != 0.0);
         }
         nz = warp_sum_ll(nz);
-        if (lane == 0 && nz)
-            atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0), (unsigned long long)nz);
+        if (lane == 0 && nz) atomicAdd(reinterpret_cast<unsigned long long *>(&s_sum), (unsigned long long)nz);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_sum)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0), (unsigned long long)s_sum);
     }
     if (!grid_barrier(a, bar++)) return;
     for (int p = threadIdx.x; p < a.P; p += THREADS) {
@@ -257,24 +483,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
             const SegList L = my_segments(a, true);
             for (int s = 0; s < L.count; ++s) {
                 const Segment sg = L.segs ? L.segs[s] : L.one;
-                if (s_status[sg.prob] != kRunning) continue;
-                const ProblemDev &P = problem(a, sg.prob);
-                const bool use_fp = P.pad != 0;
-                if (use_fp) {
-                    __syncthreads();
-                    const int4 *src = reinterpret_cast<const int4 *>(P.fp);
-                    int4 *dst = reinterpret_cast<int4 *>(s_fp);
-                    const int n16 = (P.m + 15) >> 4;
-                    for (int q = threadIdx.x; q < n16; q += THREADS) dst[q] = __ldcg(src + q);
-                    __syncthreads();
-                }
-                unsigned long long *acc_slot = &P.ctrl->acc[g & 3];
-                for (int t = sg.lo + warp; t < sg.hi; t += kWarps) {
-                    const bool acc = score_tile<DMAX>(a, P, t, use_fp ? s_fp : nullptr, stage, lane);
-                    const unsigned bal = __ballot_sync(0xffffffffu, acc);
-                    if (lane == 0 && bal) atomicAdd(acc_slot, (unsigned long long)__popc(bal));
-                }
+                if (s_status[sg.prob] != kRunning || sg.hi <= sg.lo) continue;
+                score_segment<DMAX>(a, problem(a, sg.prob), sg, g, S, chunk_seq, fp_seq, ok);
+                if (!__syncthreads_and(ok)) break;
             }
+        }
+        if (!__syncthreads_and(ok)) {
+            // a TMA wait ran out: give copies still in flight time to land, then leave
+            if (threadIdx.x == 0) {
+                const unsigned long long t0 = globaltimer();
+                while (globaltimer() - t0 < 2000000ull) __nanosleep(1000);
+            }
+            __syncthreads();
+            return;
         }
         const bool skip = (a.debug_flags & kFlagSkipArrive) && blockIdx.x == 0 && g == 0;
         if (!grid_barrier(a, bar++, !skip) || skip) return;
@@ -286,12 +507,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
                 const Segment sg = L.segs ? L.segs[s] : L.one;
                 if (s_status[sg.prob] != kRunning) continue;
                 const ProblemDev &P = problem(a, sg.prob);
+                if (threadIdx.x == 0) s_sum = 0;
+                __syncthreads();
                 for (int t = sg.lo + warp; t < sg.hi; t += kWarps) {
                     const long long delta = residual_tile(P, t, lane);
                     if (lane == 0 && delta)
-                        atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0),
-                                  (unsigned long long)delta);
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&s_sum), (unsigned long long)delta);
                 }
+                __syncthreads();  // one global atomic per CTA and segment
+                if (threadIdx.x == 0 && s_sum)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0),
+                              (unsigned long long)s_sum);
             }
         }
         if (!grid_barrier(a, bar++)) return;
@@ -323,9 +549,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
 // Host side
 // ---------------------------------------------------------------------------
 
-constexpr int kSmemLimit = 227 * 1024;
-
-static int stride_for(int dmax) { return dmax | 1; }
 static int threads_for(int dmax) { return dmax <= 8 ? 1024 : 512; }
 
 typedef void (*engine_fn)(const EngineArgs);
@@ -352,11 +575,16 @@ static engine_fn engine_kernel(int dmax) {
     }
 }
 
-// Fixed engine bytes of the workspace for P problems.
-size_t engine_ws_bytes(int P) {
-    size_t b = 0;
-    b += align_up(sizeof(unsigned) * 2, 256);                           // arrive, error
-    b += align_up(sizeof(unsigned long long) * (3 * kMaxStampIters + 2), 256);  // stamps
+static size_t stamps_bytes() {
+    return align_up(sizeof(unsigned long long) * (kSubBase + 3 * kMaxStampIters), 256);
+}
+
+static size_t sync_bytes(int P) {
+    return align_up(sizeof(EngineSync) + sizeof(DecodeCtrl) * (size_t)P, 256);
+}
+
+size_t engine_header_bytes(int P) {
+    size_t b = sync_bytes(P) + stamps_bytes();
     if (P > 1) {
         b += align_up(sizeof(ProblemDev) * (size_t)P, 256);
         b += 2 * align_up(sizeof(int) * (kMaxBlocks + 1), 256);
@@ -365,24 +593,64 @@ size_t engine_ws_bytes(int P) {
     return b;
 }
 
+DecodeCtrl *header_ctrl(char *ws, int p) {
+    return reinterpret_cast<DecodeCtrl *>(ws + sizeof(EngineSync)) + p;
+}
+
 struct DeviceInfo {
     int sms = 0;
     int coop = 0;
 };
 
-static DeviceInfo device_info() {
+static DeviceInfo device_info(int dev) {
     static std::mutex mu;
-    static int cached_dev = -1;
-    static DeviceInfo cached;
-    int dev = 0;
-    cudaGetDevice(&dev);
+    static std::map<int, DeviceInfo> cache;
     std::lock_guard<std::mutex> lk(mu);
-    if (dev != cached_dev) {
-        cudaDeviceGetAttribute(&cached.sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaDeviceGetAttribute(&cached.coop, cudaDevAttrCooperativeLaunch, dev);
-        cached_dev = dev;
-    }
-    return cached;
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    DeviceInfo di;
+    cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&di.coop, cudaDevAttrCooperativeLaunch, dev);
+    cache[dev] = di;
+    return di;
+}
+
+// Largest dynamic shared memory a launch of `fn` may use on `dev`: the
+// device's opt-in limit per CTA minus the kernel's static shared memory.
+// The kernel's attribute is raised to it once, so every later launch of any
+// size up to it is allowed.  Returns 0 on failure.
+static size_t max_dynamic_smem(int dev, engine_fn fn) {
+    static std::mutex mu;
+    static std::map<std::pair<int, void *>, size_t> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(dev, (void *)fn);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, fn) != cudaSuccess)
+        return 0;
+    const size_t lim = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim) != cudaSuccess)
+        return 0;
+    cache[key] = lim;
+    return lim;
+}
+
+// Resident CTAs per SM for (kernel, dynamic smem), cached.
+static int blocks_per_sm(int dev, engine_fn fn, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, void *, size_t>, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_tuple(dev, (void *)fn, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess)
+        return -1;
+    cache[key] = per_sm;
+    return per_sm;
 }
 
 // Split P problems' tiles (weight w_p each) into G contiguous shares.
@@ -418,44 +686,66 @@ static void partition(const std::vector<long long> &tiles, const std::vector<int
     ptr[G] = (int)segs.size();
 }
 
-// Launch the engine on P problems whose workspaces are already carved out in
-// `pds`; `eng` points at the engine area.  Fills out[0..P).
-int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *out, char *eng,
+// Launch the engine on P problems whose arrays are already carved out in
+// `pds` (ctrl pointers into the header of `ws`).  Fills out[0..P).
+int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *out, char *ws,
                cudaStream_t s) {
     const int P = (int)pds.size();
     int dmax = 1;
-    for (auto &pd : pds) dmax = std::max(dmax, pd.d);
+    bool aligned = true;
+    for (auto &pd : pds) {
+        dmax = std::max(dmax, pd.d);
+        aligned &= (reinterpret_cast<uintptr_t>(pd.csc_rows) & 15u) == 0;
+    }
+    if (!aligned) {
+        set_last_error("csc_rows must be 16-byte aligned for the persistent engine");
+        return CCS_EINVAL;
+    }
     engine_fn fn = engine_kernel(dmax);
     const int threads = threads_for(dmax);
-    const int stride = stride_for(dmax);
-    const size_t stage_bytes = (size_t)(threads / 32) * kTile * stride * 4;
+    const int warps = threads / 32;
+    int dev = 0;
+    CCS_CUDA_TRY(cudaGetDevice(&dev));
+    const size_t smem_limit = max_dynamic_smem(dev, fn);
+    if (smem_limit == 0) {
+        set_last_error("could not size the engine's shared memory");
+        return CCS_ECUDA;
+    }
+    const size_t stage_bytes = align_up((size_t)(warps - 1) * kTile * dmax * 4, 128);
+    const size_t entry = (size_t)(dmax + 1) * 4;  // one queued candidate
     const size_t status_bytes = align_up((size_t)P, 16);
-    if (stage_bytes + status_bytes + 1024 > (size_t)kSmemLimit) {
+    const size_t fixed = status_bytes + 256 + kMinQueue * entry;
+    if (fixed + 2 * stage_bytes > smem_limit) {
         set_last_error("too many problems in one launch (%d)", P);
         return CCS_EINVAL;
     }
-    const size_t fp_budget = (size_t)kSmemLimit - stage_bytes - status_bytes - 1024;
+    // fingerprints in shared memory when they leave room for >= 2 CSC stages
+    const size_t fp_budget = smem_limit - fixed - 2 * stage_bytes;
     size_t fp_cap = 0;
     for (auto &pd : pds) {
         const size_t need = align_up((size_t)pd.m, 16);
         pd.pad = need <= fp_budget ? 1 : 0;
         if (pd.pad) fp_cap = std::max(fp_cap, need);
     }
-    const size_t smem = fp_cap + stage_bytes + status_bytes;
+    fp_cap = align_up(fp_cap, 128);
+    const int stages =
+        (int)std::min<size_t>(kMaxStages, (smem_limit - fixed - fp_cap) / stage_bytes);
+    const size_t left = smem_limit - fp_cap - (size_t)stages * stage_bytes - status_bytes - 256;
+    const int queue_cap = (int)std::min<size_t>(kQueueCap, left / entry);
+    const size_t smem = fp_cap + (size_t)stages * stage_bytes + (size_t)queue_cap * entry +
+                        status_bytes;
 
-    const DeviceInfo di = device_info();
+    const DeviceInfo di = device_info(dev);
     if (!di.coop) {
         set_last_error("device does not support cooperative launches");
         return CCS_ECUDA;
     }
-    CCS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    CCS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
+    const int per_sm = blocks_per_sm(dev, fn, threads, smem);
     if (per_sm < 1) {
         set_last_error("engine kernel does not fit on an SM (smem %zu)", smem);
         return CCS_ECUDA;
     }
-    const int G = std::min(kMaxBlocks, di.sms * std::min(per_sm, 1));
+    const int G = std::min(kMaxBlocks, di.sms);
 
     EngineArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -464,21 +754,20 @@ int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *
     a.mode = prm.score_mode;
     a.max_iter = prm.max_iter;
     a.fp_cap = (int)fp_cap;
-    a.stride = stride;
+    a.stages = stages;
+    a.stage_bytes = (int)stage_bytes;
+    a.queue_cap = queue_cap;
     a.watchdog_ns = (long long)(prm.watchdog_ms > 0 ? prm.watchdog_ms : 2000) * 1000000ll;
     a.debug_flags = prm.debug_flags;
-
-    char *e = eng;
-    a.arrive = reinterpret_cast<unsigned *>(e);
-    a.error = reinterpret_cast<int *>(e + sizeof(unsigned));
-    e += align_up(sizeof(unsigned) * 2, 256);
+    a.sync = reinterpret_cast<EngineSync *>(ws);
+    char *e = ws + sync_bytes(P);
     unsigned long long *stamps = reinterpret_cast<unsigned long long *>(e);
-    e += align_up(sizeof(unsigned long long) * (3 * kMaxStampIters + 2), 256);
+    e += stamps_bytes();
     a.stamps = profiling() ? stamps : nullptr;
+    if (a.stamps) CCS_CUDA_TRY(cudaMemsetAsync(stamps, 0, stamps_bytes(), s));
 
-    // control blocks and barrier state start at zero
-    for (auto &pd : pds) CCS_CUDA_TRY(cudaMemsetAsync(pd.ctrl, 0, sizeof(DecodeCtrl), s));
-    CCS_CUDA_TRY(cudaMemsetAsync(eng, 0, sizeof(unsigned) * 2, s));
+    // barrier state and control blocks start at zero
+    CCS_CUDA_TRY(cudaMemsetAsync(ws, 0, sync_bytes(P), s));
 
     if (P == 1) {
         a.single = pds[0];
@@ -529,29 +818,32 @@ int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *
     prof_stop(ev, s);
     count_launches(1);
 
-    // results
-    std::vector<DecodeCtrl> hc(P);
-    for (int p = 0; p < P; ++p)
-        CCS_CUDA_TRY(cudaMemcpyAsync(&hc[p], pds[p].ctrl, sizeof(DecodeCtrl),
-                                     cudaMemcpyDeviceToHost, s));
-    int herr = 0;
-    CCS_CUDA_TRY(cudaMemcpyAsync(&herr, a.error, sizeof(int), cudaMemcpyDeviceToHost, s));
+    // results: one copy of the sync word and every control block
+    std::vector<char> hdr(sizeof(EngineSync) + sizeof(DecodeCtrl) * (size_t)P);
+    CCS_CUDA_TRY(cudaMemcpyAsync(hdr.data(), ws, hdr.size(), cudaMemcpyDeviceToHost, s));
     std::vector<unsigned long long> hst;
     if (a.stamps) {
-        hst.resize(3 * kMaxStampIters + 2);
+        hst.resize(kSubBase + 3 * kMaxStampIters);
         CCS_CUDA_TRY(cudaMemcpyAsync(hst.data(), stamps, sizeof(unsigned long long) * hst.size(),
                                      cudaMemcpyDeviceToHost, s));
     }
     CCS_CUDA_TRY(cudaStreamSynchronize(s));
+    EngineSync hs;
+    std::memcpy(&hs, hdr.data(), sizeof(hs));
+    const int herr = hs.error;
     int max_it = 0;
     for (int p = 0; p < P; ++p) {
-        out[p].status = hc[p].status;
-        out[p].iterations = hc[p].iteration;
-        out[p].r0_final = hc[p].r0;
+        DecodeCtrl hc;
+        std::memcpy(&hc, hdr.data() + sizeof(EngineSync) + sizeof(DecodeCtrl) * (size_t)p,
+                    sizeof(hc));
+        out[p].status = hc.status;
+        out[p].iterations = hc.iteration;
+        out[p].r0_final = hc.r0;
         out[p].error = herr ? CCS_ETIMEOUT : CCS_OK;
         out[p].reserved = 0;
-        max_it = std::max(max_it, hc[p].iteration);
+        max_it = std::max(max_it, hc.iteration);
     }
+    if (a.stamps) prof_keep_stamps(hst.data(), (int)hst.size(), kSubBase);
     if (a.stamps && !herr) {
         // barrier 0 ends init; iteration g: score ends at 1+2g, residual at 2+2g
         for (int g = 0; g < max_it && 2 + 2 * g < (int)hst.size(); ++g) {
@@ -559,11 +851,20 @@ int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *
             if (t1 >= t0 && t2 >= t1 && t0) {
                 prof_add(CCS_K_SCORE, (t1 - t0) * 1e-6);
                 prof_add(CCS_K_RESIDUAL, (t2 - t1) * 1e-6);
+                // CTA 0's view of the score phase: fingerprints in, stream
+                // done, queue done (0 when it had nothing to score)
+                const unsigned long long f = hst[kSubBase + 3 * g], st = hst[kSubBase + 3 * g + 1],
+                                         q = hst[kSubBase + 3 * g + 2];
+                if (f >= t0 && st >= f && q >= st && q <= t1) {
+                    prof_add(CCS_K_PHASE_FP, (f - t0) * 1e-6);
+                    prof_add(CCS_K_PHASE_STREAM, (st - f) * 1e-6);
+                    prof_add(CCS_K_PHASE_QUEUE, (q - st) * 1e-6);
+                }
             }
         }
     }
     if (herr) {
-        set_last_error("a grid barrier wait exceeded the watchdog (%d ms)",
+        set_last_error("a bounded device wait exceeded the watchdog (%d ms)",
                        prm.watchdog_ms > 0 ? prm.watchdog_ms : 2000);
         return CCS_ETIMEOUT;
     }

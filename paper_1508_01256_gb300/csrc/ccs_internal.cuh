@@ -11,7 +11,8 @@
 namespace ccs {
 
 constexpr int kMaxD = 16;           // register-resident gather of d <= 16 values
-constexpr int kSlots = 16;          // contributor slots kept per row
+constexpr int kSlots = 15;          // contributor slots kept per row (+1 count word)
+constexpr int kSlotRec = 16;        // ints per row record: count, then kSlots columns
 constexpr int kMaxSortRow = 32768;  // longest CSR row sorted on chip
 constexpr int kRunning = -1;        // DecodeCtrl::status while iterating
 
@@ -45,14 +46,16 @@ struct ProblemDev {
     DecodeCtrl *ctrl;
     uint8_t *touched;     // m: rows whose sum must be recomputed
     uint8_t *in_slots;    // n: column already entered in its rows' slots
-    int32_t *slot_cnt;    // m: columns entered in the row's slots
-    int32_t *slots;       // m * kSlots: those columns, unordered
+    int32_t *slots;       // m * kSlotRec: per row, one 64-byte record holding the
+                          // number of columns entered and (up to kSlots of)
+                          // those columns, unordered
     uint8_t *fp;          // m: 8-bit fingerprint of r_i (0 iff r_i == 0)
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Workspace carve-up of one decode problem: returns bytes used from `base`.
+// Workspace carve-up of one problem's arrays (its control block lives in the
+// workspace header, see engine_header_bytes): returns bytes used from `base`.
 __host__ inline size_t decode_ws_layout(int n, int m, ProblemDev *pd, char *base) {
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -60,22 +63,28 @@ __host__ inline size_t decode_ws_layout(int n, int m, ProblemDev *pd, char *base
         off = align_up(off + bytes, 256);
         return p;
     };
-    char *ctrl = take(sizeof(DecodeCtrl));
     char *touched = take((size_t)m);
     char *in_slots = take((size_t)n);
-    char *slot_cnt = take((size_t)m * 4);
-    char *slots = take((size_t)m * kSlots * 4);
+    char *slots = take((size_t)m * kSlotRec * 4);
     char *fp = take((size_t)m + 16);
     if (pd) {
         pd->fp = reinterpret_cast<uint8_t *>(fp);
-        pd->ctrl = reinterpret_cast<DecodeCtrl *>(ctrl);
         pd->touched = reinterpret_cast<uint8_t *>(touched);
         pd->in_slots = reinterpret_cast<uint8_t *>(in_slots);
-        pd->slot_cnt = reinterpret_cast<int32_t *>(slot_cnt);
         pd->slots = reinterpret_cast<int32_t *>(slots);
     }
     return off;
 }
+
+// Workspace header shared by every decode call: launch-wide sync words and
+// the P control blocks (contiguous, so one memset clears them and one copy
+// reads every result back), then engine scratch.
+struct alignas(64) EngineSync {
+    unsigned arrive;  // monotonic grid-barrier counter
+    int error;        // ErrorBits of the launch
+    int pad[14];
+};
+static_assert(sizeof(EngineSync) == 64, "EngineSync layout");
 
 // ---- binary64 bit helpers ------------------------------------------------
 
@@ -121,13 +130,16 @@ int prof_start(int kind, cudaStream_t s);
 void prof_stop(int slot, cudaStream_t s);
 void prof_collect();
 void prof_add(int kind, double ms);
+void prof_keep_stamps(const unsigned long long *st, int count, int sub_base);
 
 // host-driven loop (ccs_decode.cu)
 int decode_host_loop(const ProblemDev &P, const ccs_params &p, ccs_result *out, cudaStream_t s);
 
-// persistent engine (ccs_engine.cu)
-size_t engine_ws_bytes(int P);
-int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *out, char *eng,
+// persistent engine (ccs_engine.cu).  The workspace starts with
+// engine_header_bytes(P) bytes: EngineSync, P DecodeCtrl, engine scratch.
+size_t engine_header_bytes(int P);
+DecodeCtrl *header_ctrl(char *ws, int p);
+int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *out, char *ws,
                cudaStream_t s);
 int check_params(const ccs_params *p, int d);
 

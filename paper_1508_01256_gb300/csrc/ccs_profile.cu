@@ -18,6 +18,8 @@ bool g_on = false;
 std::vector<Pending> g_pending;
 std::vector<cudaEvent_t> g_free;
 ccs_kernel_time g_times[CCS_K_COUNT];
+std::vector<unsigned long long> g_stamps;  // last persistent launch, device ns
+int g_sub_base = 0;
 
 cudaEvent_t take_event() {
     if (!g_free.empty()) {
@@ -68,6 +70,12 @@ void prof_collect() {
     g_pending.clear();
 }
 
+void prof_keep_stamps(const unsigned long long *st, int count, int sub_base) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_stamps.assign(st, st + count);
+    g_sub_base = sub_base;
+}
+
 void prof_add(int kind, double ms) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_on) return;
@@ -97,3 +105,20 @@ extern "C" int ccs_profile_end(ccs_kernel_time *times) {
 }
 
 extern "C" int64_t ccs_launch_count(void) { return g_launches.load(); }
+
+extern "C" int ccs_profile_phases(int32_t iteration, double *phase_us) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!phase_us || iteration < 0) return CCS_EINVAL;
+    const size_t b0 = 2 * (size_t)iteration, b1 = b0 + 1, b2 = b0 + 2;
+    const size_t s0 = (size_t)g_sub_base + 3 * (size_t)iteration;
+    if (g_stamps.empty() || s0 + 2 >= g_stamps.size() || b2 >= (size_t)g_sub_base) return CCS_EINVAL;
+    const unsigned long long t0 = g_stamps[b0], t1 = g_stamps[b1], t2 = g_stamps[b2];
+    const unsigned long long f = g_stamps[s0], st = g_stamps[s0 + 1], q = g_stamps[s0 + 2];
+    if (!t0 || !t1 || !t2 || t1 < t0 || t2 < t1) return CCS_EINVAL;
+    phase_us[0] = (t1 - t0) * 1e-3;
+    phase_us[1] = (t2 - t1) * 1e-3;
+    phase_us[2] = (f >= t0 && f) ? (f - t0) * 1e-3 : -1.0;
+    phase_us[3] = (st >= f && f) ? (st - f) * 1e-3 : -1.0;
+    phase_us[4] = (q >= st && st) ? (q - st) * 1e-3 : -1.0;
+    return CCS_OK;
+}

@@ -320,7 +320,7 @@ void ccs_params_init(ccs_params *p) {
 size_t ccs_workspace_size(int32_t op, int32_t n, int32_t m, int32_t d) {
     if (check_sizes(n, m, d) != CCS_OK) return 0;
     if (op == CCS_OP_MAKE_EXPANDER) return make_expander_ws(n, m);
-    if (op == CCS_OP_DECODE) return decode_ws_layout(n, m, nullptr, nullptr) + engine_ws_bytes(1);
+    if (op == CCS_OP_DECODE) return engine_header_bytes(1) + decode_ws_layout(n, m, nullptr, nullptr);
     return 0;
 }
 

@@ -190,7 +190,7 @@ def test_edge_count_mode_oscillation(ccs, orc):
 
 
 def test_edge_slot_overflow_rows(ccs, orc):
-    """Rows with more than 16 nonzero contributors take the whole-row path."""
+    """Rows with more than 15 nonzero contributors take the whole-row path."""
     n, m, d = 4000, 60, 7   # k d / m ~ 47 contributors per row
     p = inputs.make_problem(n, m, d, 400, 77)
     g, ref = _decode_both(ccs, orc, p, max_iter=20)
