@@ -205,6 +205,22 @@ CCS_API int ccs_decode_parallel_l0(int32_t n, int32_t m, int32_t d,
                            void *ws, size_t ws_bytes, ccs_stream_t stream);
 
 /*
+ * ccs_decode_parallel_l0_async -- the same decode, enqueued on the stream
+ * without waiting: the persistent engine writes the ccs_result into DEVICE
+ * memory out_dev when the decode ends (error = CCS_ETIMEOUT if a bounded
+ * wait ran out).  The host-driven engine is not available here (CCS_EINVAL).
+ * The workspace and outputs must stay untouched until the stream reaches
+ * that point.  Argument checks as for ccs_decode_parallel_l0; CUDA errors of
+ * the launch itself are returned, later ones surface on the stream.
+ */
+CCS_API int ccs_decode_parallel_l0_async(int32_t n, int32_t m, int32_t d,
+                                         const int32_t *csc_rows, const int64_t *csr_ptr,
+                                         const int32_t *csr_cols, const double *y,
+                                         double *x_hat, double *r, int64_t *r0_hist,
+                                         const ccs_params *p, ccs_result *out_dev,
+                                         void *ws, size_t ws_bytes, ccs_stream_t stream);
+
+/*
  * ccs_decode_batch -- Parallel-l0 on `count` independent problems of any
  * sizes in one persistent cooperative launch (the iteration loop runs on the
  * device; each problem stops on its own rule and drops out of later
@@ -218,6 +234,12 @@ CCS_API int ccs_decode_parallel_l0(int32_t n, int32_t m, int32_t d,
 CCS_API int ccs_decode_batch(const ccs_problem *probs, int32_t count,
                      const ccs_params *p, ccs_result *out,
                      void *ws, size_t ws_bytes, ccs_stream_t stream);
+
+/* ccs_decode_batch enqueued without waiting; results (count entries) go to
+ * DEVICE memory out_dev, as for ccs_decode_parallel_l0_async. */
+CCS_API int ccs_decode_batch_async(const ccs_problem *probs, int32_t count,
+                                   const ccs_params *p, ccs_result *out_dev,
+                                   void *ws, size_t ws_bytes, ccs_stream_t stream);
 
 /* ---- measurement hooks ---------------------------------------------------
  * Kernel timing for benchmarks: between ccs_profile_begin() and

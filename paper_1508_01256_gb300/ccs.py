@@ -102,6 +102,10 @@ def lib() -> ctypes.CDLL:
                                              P, sz, P]
         l.ccs_decode_batch.argtypes = [ctypes.POINTER(Problem), i32, ctypes.POINTER(Params),
                                        ctypes.POINTER(Result), P, sz, P]
+        l.ccs_decode_parallel_l0_async.argtypes = [i32, i32, i32, P, P, P, P, P, P, P,
+                                                   ctypes.POINTER(Params), P, P, sz, P]
+        l.ccs_decode_batch_async.argtypes = [ctypes.POINTER(Problem), i32, ctypes.POINTER(Params),
+                                             P, P, sz, P]
         l.ccs_profile_begin.argtypes = []
         l.ccs_profile_end.argtypes = [ctypes.POINTER(KernelTime)]
         l.ccs_profile_phases.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
@@ -109,7 +113,8 @@ def lib() -> ctypes.CDLL:
         l.ccs_launch_count.argtypes = []
         l.ccs_launch_count.restype = ctypes.c_int64
         for name in ("ccs_make_expander", "ccs_measure", "ccs_decode_parallel_l0",
-                     "ccs_decode_batch", "ccs_profile_begin", "ccs_profile_end"):
+                     "ccs_decode_batch", "ccs_profile_begin", "ccs_profile_end",
+                     "ccs_decode_parallel_l0_async", "ccs_decode_batch_async"):
             getattr(l, name).restype = ctypes.c_int
         _lib = l
         return l
@@ -187,6 +192,40 @@ def ccs_decode_parallel_l0(n, m, d, csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0
         _ptr(ws), ws.numel() * ws.element_size(), _stream(stream))
     _check(rc, "ccs_decode_parallel_l0")
     return out
+
+
+def ccs_decode_parallel_l0_async(n, m, d, csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist,
+                                 p: Params | None, out_dev, ws, stream=None):
+    """Enqueue a decode; its ccs_result lands in the device buffer out_dev
+    (a tensor of >= RESULT_BYTES bytes, or a device address)."""
+    rc = lib().ccs_decode_parallel_l0_async(
+        n, m, d, _ptr(csc_rows), _ptr(csr_ptr), _ptr(csr_cols), _ptr(y), _ptr(x_hat), _ptr(r),
+        _ptr(r0_hist), ctypes.byref(p) if p is not None else None, _ptr(out_dev),
+        _ptr(ws), ws.numel() * ws.element_size(), _stream(stream))
+    _check(rc, "ccs_decode_parallel_l0_async")
+
+
+def ccs_decode_batch_async(probs, p: Params | None, out_dev, ws, stream=None):
+    cnt = len(probs)
+    arr = (Problem * cnt)(*probs)
+    rc = lib().ccs_decode_batch_async(arr, cnt, ctypes.byref(p) if p is not None else None,
+                                      _ptr(out_dev), _ptr(ws), ws.numel() * ws.element_size(),
+                                      _stream(stream))
+    _check(rc, "ccs_decode_batch_async")
+
+
+RESULT_BYTES = ctypes.sizeof(Result)
+
+
+def result_buffer(count: int, device="cuda"):
+    """Device buffer for `count` ccs_result records."""
+    import torch
+    return torch.zeros(count * RESULT_BYTES, dtype=torch.uint8, device=device)
+
+
+def results_from_device(buf, count: int) -> list[Result]:
+    raw = bytes(buf[:count * RESULT_BYTES].cpu().numpy().tobytes())
+    return [Result.from_buffer_copy(raw, i * RESULT_BYTES) for i in range(count)]
 
 
 def ccs_decode_batch(probs, p: Params | None, ws, stream=None) -> list[Result]:

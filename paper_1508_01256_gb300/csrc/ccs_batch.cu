@@ -23,9 +23,9 @@ extern "C" size_t ccs_batch_workspace_size(const ccs_problem *probs, int32_t cou
     return batch_ws(probs, count);
 }
 
-extern "C" int ccs_decode_batch(const ccs_problem *probs, int32_t count, const ccs_params *params,
-                                ccs_result *out, void *ws, size_t ws_bytes,
-                                ccs_stream_t stream) {
+static int decode_batch_impl(const ccs_problem *probs, int32_t count, const ccs_params *params,
+                             ccs_result *out, void *ws, size_t ws_bytes, ccs_stream_t stream,
+                             ccs_result *dev_out) {
     if (!probs || count < 1 || !out || !ws) {
         set_last_error("ccs_decode_batch: bad arguments");
         return CCS_EINVAL;
@@ -72,6 +72,10 @@ extern "C" int ccs_decode_batch(const ccs_problem *probs, int32_t count, const c
         base += decode_ws_layout(pr.n, pr.m, &P, base);
     }
     if (p.engine == CCS_ENGINE_HOST_LOOP) {
+        if (dev_out) {
+            set_last_error("ccs_decode_batch_async: the host-driven engine cannot run asynchronously");
+            return CCS_EINVAL;
+        }
         // one decode after another, each with its own launches
         for (int32_t q = 0; q < count; ++q) {
             rc = decode_host_loop(pds[q], p, &out[q], s);
@@ -79,5 +83,22 @@ extern "C" int ccs_decode_batch(const ccs_problem *probs, int32_t count, const c
         }
         return CCS_OK;
     }
-    return engine_run(pds, p, out, hdr, s);
+    return engine_run(pds, p, out, hdr, s, dev_out);
+}
+
+extern "C" int ccs_decode_batch(const ccs_problem *probs, int32_t count, const ccs_params *params,
+                                ccs_result *out, void *ws, size_t ws_bytes,
+                                ccs_stream_t stream) {
+    return decode_batch_impl(probs, count, params, out, ws, ws_bytes, stream, nullptr);
+}
+
+extern "C" int ccs_decode_batch_async(const ccs_problem *probs, int32_t count,
+                                      const ccs_params *params, ccs_result *out_dev, void *ws,
+                                      size_t ws_bytes, ccs_stream_t stream) {
+    if (!out_dev) {
+        set_last_error("ccs_decode_batch_async: null result pointer");
+        return CCS_EINVAL;
+    }
+    std::vector<ccs_result> unused(count > 0 ? count : 1);
+    return decode_batch_impl(probs, count, params, unused.data(), ws, ws_bytes, stream, out_dev);
 }

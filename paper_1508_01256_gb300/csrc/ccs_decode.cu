@@ -212,32 +212,28 @@ int decode_host_loop(const ProblemDev &P, const ccs_params &p, ccs_result *out,
     return out->error;
 }
 
-}  // namespace ccs
 
-using namespace ccs;
-
-extern "C" int ccs_decode_parallel_l0(int32_t n, int32_t m, int32_t d, const int32_t *csc_rows,
-                                      const int64_t *csr_ptr, const int32_t *csr_cols,
-                                      const double *y, double *x_hat, double *r,
-                                      int64_t *r0_hist, const ccs_params *params,
-                                      ccs_result *out, void *ws, size_t ws_bytes,
-                                      ccs_stream_t stream) {
+// Shared set-up of the blocking and asynchronous single-problem calls.
+static int decode_setup(int32_t n, int32_t m, int32_t d, const int32_t *csc_rows,
+                        const int64_t *csr_ptr, const int32_t *csr_cols, const double *y,
+                        double *x_hat, double *r, int64_t *r0_hist, const ccs_params *params,
+                        void *out, void *ws, size_t ws_bytes, const char *who, ccs_params &p,
+                        ProblemDev &P) {
     int rc = check_sizes(n, m, d);
     if (rc) return rc;
-    ccs_params p;
     if (params) p = *params;
     else ccs_params_init(&p);
     if ((rc = check_params(&p, d))) return rc;
     if (!csc_rows || !csr_ptr || !csr_cols || !y || !x_hat || !r || !out || !ws) {
-        set_last_error("ccs_decode_parallel_l0: null pointer argument");
+        set_last_error("%s: null pointer argument", who);
         return CCS_EINVAL;
     }
     const size_t need = engine_header_bytes(1) + decode_ws_layout(n, m, nullptr, nullptr);
     if (ws_bytes < need) {
-        set_last_error("ccs_decode_parallel_l0: workspace %zu < %zu bytes", ws_bytes, need);
+        set_last_error("%s: workspace %zu < %zu bytes", who, ws_bytes, need);
         return CCS_ENOMEM;
     }
-    ProblemDev P{};
+    P = ProblemDev{};
     P.n = n;
     P.m = m;
     P.d = d;
@@ -251,8 +247,47 @@ extern "C" int ccs_decode_parallel_l0(int32_t n, int32_t m, int32_t d, const int
     char *base = static_cast<char *>(ws);
     P.ctrl = header_ctrl(base, 0);
     decode_ws_layout(n, m, &P, base + engine_header_bytes(1));
+    return CCS_OK;
+}
+
+}  // namespace ccs
+
+using namespace ccs;
+
+extern "C" int ccs_decode_parallel_l0(int32_t n, int32_t m, int32_t d, const int32_t *csc_rows,
+                                      const int64_t *csr_ptr, const int32_t *csr_cols,
+                                      const double *y, double *x_hat, double *r,
+                                      int64_t *r0_hist, const ccs_params *params,
+                                      ccs_result *out, void *ws, size_t ws_bytes,
+                                      ccs_stream_t stream) {
+    ccs_params p;
+    ProblemDev P;
+    int rc = decode_setup(n, m, d, csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist, params, out,
+                          ws, ws_bytes, "ccs_decode_parallel_l0", p, P);
+    if (rc) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (p.engine == CCS_ENGINE_HOST_LOOP) return decode_host_loop(P, p, out, s);
     std::vector<ProblemDev> one(1, P);
-    return engine_run(one, p, out, base, s);
+    return engine_run(one, p, out, static_cast<char *>(ws), s);
+}
+
+extern "C" int ccs_decode_parallel_l0_async(int32_t n, int32_t m, int32_t d,
+                                            const int32_t *csc_rows, const int64_t *csr_ptr,
+                                            const int32_t *csr_cols, const double *y,
+                                            double *x_hat, double *r, int64_t *r0_hist,
+                                            const ccs_params *params, ccs_result *out_dev,
+                                            void *ws, size_t ws_bytes, ccs_stream_t stream) {
+    ccs_params p;
+    ProblemDev P;
+    int rc = decode_setup(n, m, d, csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist, params,
+                          out_dev, ws, ws_bytes, "ccs_decode_parallel_l0_async", p, P);
+    if (rc) return rc;
+    if (p.engine == CCS_ENGINE_HOST_LOOP) {
+        set_last_error("ccs_decode_parallel_l0_async: the host-driven engine cannot run asynchronously");
+        return CCS_EINVAL;
+    }
+    std::vector<ProblemDev> one(1, P);
+    ccs_result unused;
+    return engine_run(one, p, &unused, static_cast<char *>(ws),
+                      reinterpret_cast<cudaStream_t>(stream), out_dev);
 }

@@ -70,6 +70,7 @@ struct EngineArgs {
     unsigned long long *stamps; // globaltimer after each barrier (or null)
     long long watchdog_ns;
     int debug_flags;
+    ccs_result *dev_out;        // per-problem results in device memory (or null)
 };
 
 // ---- device helpers --------------------------------------------------------
@@ -174,6 +175,12 @@ __device__ bool grid_barrier(const EngineArgs &a, unsigned index, bool arrive = 
 
 __device__ __forceinline__ const ProblemDev &problem(const EngineArgs &a, int p) {
     return a.probs ? a.probs[p] : a.single;
+}
+
+// A CTA that leaves early (a wait ran out) marks every device-side result.
+__device__ __forceinline__ void fail_out(const EngineArgs &a) {
+    if (a.dev_out && threadIdx.x == 0)
+        for (int p = 0; p < a.P; ++p) a.dev_out[p].error = CCS_ETIMEOUT;
 }
 
 // This CTA's segments of a phase.  One problem: a contiguous share of its
@@ -456,7 +463,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
         if (threadIdx.x == 0 && s_sum)
             atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0), (unsigned long long)s_sum);
     }
-    if (!grid_barrier(a, bar++)) return;
+    if (!grid_barrier(a, bar++)) {
+        fail_out(a);
+        return;
+    }
     for (int p = threadIdx.x; p < a.P; p += THREADS) {
         const ProblemDev &P = problem(a, p);
         const long long r0 = __ldcg(&P.ctrl->r0);
@@ -495,10 +505,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
                 while (globaltimer() - t0 < 2000000ull) __nanosleep(1000);
             }
             __syncthreads();
+            fail_out(a);
             return;
         }
         const bool skip = (a.debug_flags & kFlagSkipArrive) && blockIdx.x == 0 && g == 0;
-        if (!grid_barrier(a, bar++, !skip) || skip) return;
+        if (!grid_barrier(a, bar++, !skip) || skip) {
+            fail_out(a);
+            return;
+        }
 
         // ---- residual + ||r||_0 ---------------------------------------------
         {
@@ -520,7 +534,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
                               (unsigned long long)s_sum);
             }
         }
-        if (!grid_barrier(a, bar++)) return;
+        if (!grid_barrier(a, bar++)) {
+            fail_out(a);
+            return;
+        }
 
         // ---- stop rule ("while not converged", three ways to stop) ----------
         for (int p = threadIdx.x; p < a.P; p += THREADS) {
@@ -542,6 +559,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
             if (blockIdx.x == 0 && st != kRunning) P.ctrl->status = st;
         }
         __syncthreads();
+    }
+    // every problem has stopped: CTA 0 publishes the results on the device
+    if (a.dev_out && blockIdx.x == 0) {
+        for (int p = threadIdx.x; p < a.P; p += THREADS) {
+            const ProblemDev &P = problem(a, p);
+            ccs_result res;
+            res.status = P.ctrl->status;
+            res.iterations = P.ctrl->iteration;
+            res.r0_final = __ldcg(&P.ctrl->r0);
+            res.error = __ldcg(&a.sync->error) ? CCS_ETIMEOUT : CCS_OK;
+            res.reserved = 0;
+            a.dev_out[p] = res;
+        }
     }
 }
 
@@ -689,7 +719,7 @@ static void partition(const std::vector<long long> &tiles, const std::vector<int
 // Launch the engine on P problems whose arrays are already carved out in
 // `pds` (ctrl pointers into the header of `ws`).  Fills out[0..P).
 int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *out, char *ws,
-               cudaStream_t s) {
+               cudaStream_t s, ccs_result *dev_out) {
     const int P = (int)pds.size();
     int dmax = 1;
     bool aligned = true;
@@ -763,7 +793,8 @@ int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *
     char *e = ws + sync_bytes(P);
     unsigned long long *stamps = reinterpret_cast<unsigned long long *>(e);
     e += stamps_bytes();
-    a.stamps = profiling() ? stamps : nullptr;
+    a.stamps = (profiling() && !dev_out) ? stamps : nullptr;
+    a.dev_out = dev_out;
     if (a.stamps) CCS_CUDA_TRY(cudaMemsetAsync(stamps, 0, stamps_bytes(), s));
 
     // barrier state and control blocks start at zero
@@ -817,6 +848,7 @@ int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *
     CCS_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)fn, dim3(G), dim3(threads), args, smem, s));
     prof_stop(ev, s);
     count_launches(1);
+    if (dev_out) return CCS_OK;  // asynchronous: the kernel writes the results
 
     // results: one copy of the sync word and every control block
     std::vector<char> hdr(sizeof(EngineSync) + sizeof(DecodeCtrl) * (size_t)P);

@@ -319,3 +319,65 @@ def test_batch_order_does_not_matter(ccs):
         assert a.status == b.status and a.iterations == b.iterations
         assert np.array_equal(a.x_hat.cpu().numpy(), b.x_hat.cpu().numpy())
         assert np.array_equal(a.r.cpu().numpy(), b.r.cpu().numpy())
+
+
+def test_async_decode_matches_blocking(ccs, orc):
+    """ccs_decode_parallel_l0_async: results land in device memory, several
+    decodes queued back to back on one stream without a host wait."""
+    import torch
+    probs = [inputs.plain_small(seed=s) for s in range(3)] + \
+        [inputs.make_problem(50000, 5000, 9, 600, 71)]
+    items = [device_problem(ccs, p) for p in probs]
+    res_dev = ccs.result_buffer(len(probs))
+    outs = []
+    for i, (p, (csc, ptr, cols, y)) in enumerate(zip(probs, items)):
+        x_hat = torch.empty(p.n, dtype=torch.float64, device="cuda")
+        r = torch.empty(p.m, dtype=torch.float64, device="cuda")
+        ws = ccs.workspace(ccs.ccs_workspace_size(ccs.OP_DECODE, p.n, p.m, p.d))
+        ccs.ccs_decode_parallel_l0_async(p.n, p.m, p.d, csc, ptr, cols, y, x_hat, r, None,
+                                         ccs.params(), res_dev[i * ccs.RESULT_BYTES:], ws)
+        outs.append((x_hat, r, ws))
+    torch.cuda.synchronize()
+    res = ccs.results_from_device(res_dev, len(probs))
+    for p, (x_hat, r, _), rr in zip(probs, outs, res):
+        A, y_ref = oracle_problem(orc, p)
+        ref = orc.parallel_l0(A, p.m, y_ref)
+        assert rr.error == 0 and rr.status == ref["status"]
+        assert rr.iterations == ref["iterations"] and rr.r0_final == ref["r0_final"]
+        assert np.array_equal(x_hat.cpu().numpy(), ref["x_hat"])
+        assert np.array_equal(r.cpu().numpy(), ref["r"])
+
+
+def test_async_batch_matches_oracle(ccs, orc):
+    import torch
+    probs = inputs.batch_problems(16, seed=91, log2n_hi=15.0)
+    items = [device_problem(ccs, p) for p in probs]
+    pbs, outs = [], []
+    for (csc, ptr, cols, y), p in zip(items, probs):
+        x_hat = torch.empty(p.n, dtype=torch.float64, device="cuda")
+        r = torch.empty(p.m, dtype=torch.float64, device="cuda")
+        outs.append((x_hat, r))
+        pbs.append(ccs.problem(csc, ptr, cols, y, x_hat, r))
+    ws = ccs.workspace(ccs.ccs_batch_workspace_size(pbs))
+    res_dev = ccs.result_buffer(len(pbs))
+    ccs.ccs_decode_batch_async(pbs, ccs.params(), res_dev, ws)
+    torch.cuda.synchronize()
+    for p, (x_hat, r), rr in zip(probs, outs, ccs.results_from_device(res_dev, len(pbs))):
+        A, y_ref = oracle_problem(orc, p)
+        ref = orc.parallel_l0(A, p.m, y_ref)
+        assert rr.error == 0 and rr.status == ref["status"] and rr.iterations == ref["iterations"]
+        assert np.array_equal(x_hat.cpu().numpy(), ref["x_hat"])
+
+
+def test_async_watchdog_reports_on_device(ccs):
+    import torch
+    p = inputs.plain_small(seed=3)
+    csc, ptr, cols, y = device_problem(ccs, p)
+    x_hat = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    r = torch.empty(p.m, dtype=torch.float64, device="cuda")
+    ws = ccs.workspace(ccs.ccs_workspace_size(ccs.OP_DECODE, p.n, p.m, p.d))
+    res_dev = ccs.result_buffer(1)
+    ccs.ccs_decode_parallel_l0_async(p.n, p.m, p.d, csc, ptr, cols, y, x_hat, r, None,
+                                     ccs.params(watchdog_ms=100, debug_flags=1), res_dev, ws)
+    torch.cuda.synchronize()
+    assert ccs.results_from_device(res_dev, 1)[0].error == ccs.CCS_ETIMEOUT
