@@ -216,6 +216,69 @@ def cpu_baseline(name: str, budget_s: float = 12.0):
             "exact_recovery": exact}
 
 
+def batched_vs_plain(ccs, dev, count: int, seed: int, reps: int = 3):
+    """Decodes/s of `count` mixed problems (n log-uniform in [2^12, 2^20],
+    delta, rho, d drawn from the batched workload's sets) in ONE persistent
+    launch, against the same problems as `count` back-to-back plain
+    single-problem launches on the same stream.  L2 flushed before each."""
+    import torch
+
+    from paper_1508_01256_gb300 import inputs
+    probs = inputs.batch_problems(count, seed=seed)
+    items, pbs, outs = [], [], []
+    for p in probs:
+        csc, ptr, cols = ccs.make_expander(p.n, p.m, p.d, p.a_seed, device=dev)
+        y = ccs.measure(ptr, cols, torch.from_numpy(p.x).to(dev), p.m, p.d)
+        x_hat = torch.empty(p.n, dtype=torch.float64, device=dev)
+        r = torch.empty(p.m, dtype=torch.float64, device=dev)
+        items.append((p, csc, ptr, cols, y))
+        outs.append((x_hat, r))
+        pbs.append(ccs.problem(csc, ptr, cols, y, x_hat, r))
+    ws_b = ccs.workspace(ccs.ccs_batch_workspace_size(pbs), dev)
+    ws_p = ccs.workspace(max(ccs.ccs_workspace_size(ccs.OP_DECODE, p.n, p.m, p.d) for p in probs), dev)
+    res_b = ccs.result_buffer(count, dev)
+    res_p = ccs.result_buffer(count, dev)
+    prm = ccs.params()
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    tb, tp = [], []
+    for rep in range(reps + 1):
+        flush.zero_()
+        ev[0].record(stream)
+        ccs.ccs_decode_batch_async(pbs, prm, res_b, ws_b, stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        if rep:
+            tb.append(ev[0].elapsed_time(ev[1]))
+        flush.zero_()
+        ev[0].record(stream)
+        for i, (p, csc, ptr, cols, y) in enumerate(items):
+            x_hat, r = outs[i]
+            ccs.ccs_decode_parallel_l0_async(p.n, p.m, p.d, csc, ptr, cols, y, x_hat, r, None,
+                                             prm, res_p[i * ccs.RESULT_BYTES:], ws_p, stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        if rep:
+            tp.append(ev[0].elapsed_time(ev[1]))
+    rb = ccs.results_from_device(res_b, count)
+    rp = ccs.results_from_device(res_p, count)
+    same = all(a.status == b.status and a.iterations == b.iterations and a.r0_final == b.r0_final
+               for a, b in zip(rb, rp))
+    conv = sum(a.status == ccs.CONVERGED for a in rb)
+    exact = sum(a.status == ccs.CONVERGED and bool((outs[i][0].cpu().numpy() == items[i][0].x).all())
+                for i, a in enumerate(rb))
+    mb, mp = statistics.median(tb), statistics.median(tp)
+    cols_total = sum(p.n * a.iterations for p, a in zip(probs, rb))
+    return {"problems": count, "batched_decodes_per_s": count / (mb / 1000.0),
+            "plain_decodes_per_s": count / (mp / 1000.0), "batched_ms": mb, "plain_ms": mp,
+            "speedup": mp / mb, "batched_column_updates_per_s": cols_total / (mb / 1000.0),
+            "same_results": same, "converged": conv, "exact_recovery": exact,
+            "max_iterations": max(a.iterations for a in rb),
+            "workload": "n log-uniform 2^12..2^20, m/n in {0.01,0.05,0.1,0.3}, "
+                        "k/m in {0.05,0.1,0.2}, d in {5,7,9,11}, gauss-grid"}
+
+
 def run_reference(args):
     from paper_1508_01256_gb300 import inputs  # noqa: F401  (inputs only)
     rank = int(os.environ.get("RANK", "0"))
@@ -305,7 +368,7 @@ def run_ccs(args):
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     res_dev = ccs.result_buffer(args.steps, dev)
-    prm = ccs.params(engine=args.engine)
+    prm = ccs.params(engine=args.engine, schedule=args.schedule)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -408,6 +471,10 @@ def run_ccs(args):
                     roof["score_phase"][sub.split(".")[1] + "_us"] = 1000.0 * ms_ / n_
     kernel_share = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in ktimes.items()}
 
+    batched = None
+    if args.batch > 0:
+        batched = batched_vs_plain(ccs, dev, args.batch, seed=1000 * rank + 4242)
+
     if rank == 0:
         cb = None
         if world == 1 and not args.no_cpu_baseline:
@@ -418,6 +485,7 @@ def run_ccs(args):
                 "scaling": "weak", "vs_baseline": vs_baseline(args.workload, p0, value),
                 "dtype": "f64", "data": "synthetic",
                 "config": dict(workload_config(args.workload, p0), engine=args.engine,
+                               schedule=args.schedule,
                                l2="flushed between steps (512 MB write)",
                                parallelism=f"replicas{world}"),
                 "e2e": {"value": e2e_value, "unit": "decodes/s", "h2d_bytes_per_step": h2d,
@@ -430,6 +498,7 @@ def run_ccs(args):
                 "iterations_mean": statistics.mean(iters),
                 "exact_recovery": exact,
                 "kernel_times": kernel_share,
+                "batched": batched,
                 "wall_s_timed_region": wall}
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -445,8 +514,12 @@ def main():
     ap.add_argument("--workload", default="at-scale",
                     choices=["at-scale", "small", "extreme", "table3"])
     ap.add_argument("--engine", type=int, default=0)
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="persistent-engine launch shape (0: library's choice)")
     ap.add_argument("--instances", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=512,
+                    help="problems in the batched-vs-plain comparison (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

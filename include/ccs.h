@@ -99,7 +99,12 @@ typedef struct {
                              engine): CTA 0 skips its arrival at the first
                              score barrier, so every CTA's bounded wait runs
                              out and the call returns CCS_ETIMEOUT           */
-    int32_t reserved[2];  /* must be zero                                     */
+    int32_t schedule;     /* persistent-engine launch shape: 0 = library's
+                             choice (1 when d <= 8, else 2); 1 = 1024
+                             threads a CTA, one 32-column tile per warp and
+                             chunk (d <= 8 only); 2 = 512 threads, two
+                             tiles per warp and chunk                       */
+    int32_t reserved;     /* must be zero                                     */
 } ccs_params;
 
 typedef struct {

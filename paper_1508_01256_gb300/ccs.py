@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("score_mode", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("watchdog_ms", ctypes.c_int32), ("debug_flags", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -152,11 +152,12 @@ def _need(t, dtype, numel, name):
 
 
 def params(alpha=2, max_iter=100, score_mode=SCORE_L0_DECREASE, engine=ENGINE_AUTO,
-           watchdog_ms=0, debug_flags=0) -> Params:
+           watchdog_ms=0, debug_flags=0, schedule=0) -> Params:
     p = Params()
     lib().ccs_params_init(ctypes.byref(p))
     p.alpha, p.max_iter, p.score_mode, p.engine, p.watchdog_ms, p.debug_flags = (
         alpha, max_iter, score_mode, engine, watchdog_ms, debug_flags)
+    p.schedule = schedule
     return p
 
 

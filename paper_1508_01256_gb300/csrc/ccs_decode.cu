@@ -163,8 +163,8 @@ int check_params(const ccs_params *p, int d) {
         set_last_error("unknown engine %d", p->engine);
         return CCS_EINVAL;
     }
-    if (p->watchdog_ms < 0 || p->reserved[0] || p->reserved[1]) {
-        set_last_error("bad watchdog_ms or nonzero reserved fields");
+    if (p->watchdog_ms < 0 || p->reserved || p->schedule < 0 || p->schedule > 2) {
+        set_last_error("bad watchdog_ms, schedule or nonzero reserved field");
         return CCS_EINVAL;
     }
     return CCS_OK;

@@ -41,6 +41,7 @@ namespace ccs {
 
 constexpr int kTile = 32;
 constexpr int kMaxBlocks = 1024;
+constexpr int kMaxProblems = 4096;  // per launch: their status and weight prefix live on chip
 constexpr int kMaxStampIters = 1024;
 constexpr int kMaxStages = 6;
 constexpr int kQueueCap = 2048;     // most candidate columns queued per CTA and segment
@@ -62,10 +63,6 @@ struct EngineArgs {
     int stages;                 // CSC ring depth
     int stage_bytes;            // bytes per stage (one tile per warp)
     int queue_cap;              // candidate entries (column + its d rows)
-    const int *score_ptr;       // G+1 offsets into score_segs (batch only)
-    const Segment *score_segs;
-    const int *res_ptr;
-    const Segment *res_segs;
     EngineSync *sync;
     unsigned long long *stamps; // globaltimer after each barrier (or null)
     long long watchdog_ns;
@@ -183,32 +180,95 @@ __device__ __forceinline__ void fail_out(const EngineArgs &a) {
         for (int p = 0; p < a.P; ++p) a.dev_out[p].error = CCS_ETIMEOUT;
 }
 
-// This CTA's segments of a phase.  One problem: a contiguous share of its
-// tiles computed here; a batch: the host-built partition.
-struct SegList {
-    const Segment *segs;
-    int count;
-    Segment one;
-};
+// ---- work partition -----------------------------------------------------
+//
+// Every phase splits the tiles of the problems that are still running into
+// gridDim.x contiguous shares of equal weight.  A tile of problem p weighs
+// d_p for the score phase (its columns' row indices) and 1 for row tiles.
+// Each CTA computes the same prefix of weights over the problems in shared
+// memory and takes the tiles whose starting weight falls in its share, so
+// the shares follow the running set from one iteration to the next.
 
-__device__ __forceinline__ SegList my_segments(const EngineArgs &a, bool score) {
-    SegList L;
-    if (!a.probs) {
-        const ProblemDev &P = a.single;
-        const long long tiles = score ? (P.n + kTile - 1) / kTile : (P.m + kTile - 1) / kTile;
-        L.one.prob = 0;
-        L.one.lo = (int)(tiles * blockIdx.x / gridDim.x);
-        L.one.hi = (int)(tiles * (blockIdx.x + 1) / gridDim.x);
-        L.one.pad = 0;
-        L.segs = nullptr;
-        L.count = 1;
-    } else {
-        const int *ptr = score ? a.score_ptr : a.res_ptr;
-        L.segs = (score ? a.score_segs : a.res_segs) + ptr[blockIdx.x];
-        L.count = ptr[blockIdx.x + 1] - ptr[blockIdx.x];
-        L.one = Segment{0, 0, 0, 0};
+enum PartKind { kPartScore = 0, kPartRows = 1, kPartInitCols = 2, kPartInitRows = 3 };
+
+__device__ __forceinline__ long long part_tiles(const ProblemDev &P, int kind) {
+    return (kind == kPartScore || kind == kPartInitCols) ? (P.n + kTile - 1) / kTile
+                                                         : (P.m + kTile - 1) / kTile;
+}
+
+__device__ __forceinline__ long long part_weight(const ProblemDev &P, int kind) {
+    return kind == kPartScore ? P.d : 1;
+}
+
+// pref[0..P]: exclusive prefix of the problems' weights (0 for problems
+// that are not running, except in the init kinds).  Block-wide.
+template <int THREADS>
+__device__ __noinline__ void build_partition(const EngineArgs &a, const int8_t *status, long long *pref,
+                                int kind) {
+    __shared__ long long s_warp[THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int per = (a.P + THREADS - 1) / THREADS;
+    const int p0 = threadIdx.x * per;
+    long long mine = 0;
+    for (int q = 0; q < per; ++q) {
+        const int p = p0 + q;
+        if (p < a.P) {
+            const bool on = kind >= kPartInitCols || status[p] == kRunning;
+            if (on) {
+                const ProblemDev &P = problem(a, p);
+                mine += part_tiles(P, kind) * part_weight(P, kind);
+            }
+        }
     }
-    return L;
+    long long inc = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    __syncthreads();  // previous readers of pref / s_warp are done
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    long long before = 0;
+    for (int w = 0; w < warp; ++w) before += s_warp[w];
+    long long run = before + inc - mine;  // exclusive prefix of this thread's first element
+    for (int q = 0; q < per; ++q) {
+        const int p = p0 + q;
+        if (p < a.P) {
+            pref[p] = run;
+            const bool on = kind >= kPartInitCols || status[p] == kRunning;
+            if (on) {
+                const ProblemDev &P = problem(a, p);
+                run += part_tiles(P, kind) * part_weight(P, kind);
+            }
+        }
+    }
+    if (threadIdx.x == THREADS - 1) pref[a.P] = run;
+    __syncthreads();
+}
+
+// Visit this CTA's segments (problem, tiles [lo, hi)) of a partition.
+template <typename F>
+__device__ __forceinline__ void for_my_segments(const EngineArgs &a, const int8_t *status,
+                                                const long long *pref, int kind, F &&fn) {
+    const long long W = pref[a.P];
+    if (W == 0) return;
+    const long long B0 = W * blockIdx.x / gridDim.x, B1 = W * (blockIdx.x + 1) / gridDim.x;
+    int lo = 0, hi = a.P;  // first p with pref[p + 1] > B0
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (pref[mid + 1] > B0) hi = mid;
+        else lo = mid + 1;
+    }
+    for (int p = lo; p < a.P && pref[p] < B1; ++p) {
+        const bool on = kind >= kPartInitCols || status[p] == kRunning;
+        if (!on) continue;
+        const ProblemDev &P = problem(a, p);
+        const long long w = part_weight(P, kind), tiles = part_tiles(P, kind);
+        const long long t0 = B0 > pref[p] ? (B0 - pref[p] + w - 1) / w : 0;
+        const long long t1 = min(tiles, (B1 - pref[p] + w - 1) / w);
+        if (t1 > t0) fn(p, P, (int)t0, (int)t1);
+    }
 }
 
 // Shared-memory state of the score phase.
@@ -245,17 +305,61 @@ __device__ __forceinline__ void issue_chunk(const EngineArgs &a, const ProblemDe
     if (tma) bulk_g2s(S.stage + (size_t)slot * a.stage_bytes, P.csc_rows + col0 * P.d, tma, bar);
 }
 
+// Exact score and apply of one column inside the stream (problems without
+// shared-memory fingerprints, or a full queue).
+template <int DMAX>
+__device__ __forceinline__ bool score_inline(const EngineArgs &a, const ProblemDev &P, int j,
+                                          const int32_t (&rows)[DMAX], int d) {
+    unsigned long long omega;
+    const bool acc = exact_score<DMAX>(rows, d, P.r, a.alpha, a.mode, &omega);
+    if (acc) apply_pair<DMAX>(P, j, rows, d, omega);
+    return acc;
+}
+
+// Queued candidates: exact score, lane-parallel over the CTA.  The r
+// gathers, x_hat_j and the in-slots flag go out in one round trip.
+template <int DMAX>
+__device__ __forceinline__ void score_queue(const EngineArgs &a, const ProblemDev &P, ScoreSmem &S,
+                                         bool ok) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int d = P.d;
+    const int qn = min(*S.qn, a.queue_cap);
+    for (int b0 = warp * 32; b0 < qn; b0 += blockDim.x) {
+        const int idx = b0 + lane;
+        bool acc = false;
+        if (ok && idx < qn) {
+            const int32_t *e = S.queue + idx * (DMAX + 1);
+            const int j = e[0];
+            int32_t rows[DMAX];
+            unsigned long long v[DMAX];
+#pragma unroll
+            for (int t = 0; t < DMAX; ++t) rows[t] = e[1 + t];
+#pragma unroll
+            for (int t = 0; t < DMAX; ++t) v[t] = (t < d) ? value_bits(__ldcg(P.r + rows[t])) : 0ull;
+            const double xj = __ldcg(P.x_hat + j);
+            const uint8_t ins = __ldcg(P.in_slots + j);
+            unsigned long long omega;
+            acc = exact_score_values<DMAX>(v, d, a.alpha, a.mode, &omega);
+            if (acc) apply_pair_loaded<DMAX>(P, j, rows, d, omega, xj, ins);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, acc);
+        if (lane == 0 && bal) atomicAdd(S.acc, (unsigned long long)__popc(bal));
+    }
+}
+
 // Score phase of one segment.  Warp 0 is the producer: its lane 0 streams
 // the fingerprints and the CSC chunks by TMA, refilling a stage as soon as
 // every consumer warp has released it.  Warps 1.. consume one 32-column tile
 // of each chunk: the fingerprint bound from shared memory, candidates into
 // the queue.  Then every warp scores the queued candidates exactly.
-template <int DMAX>
+template <int DMAX, int THREADS>
 __device__ __forceinline__ void score_segment(const EngineArgs &a, const ProblemDev &P,
-                                              const Segment &sg, int g, ScoreSmem &S,
+                                              int seg_lo, int seg_hi, int g, ScoreSmem &S,
                                               unsigned &chunk_seq, unsigned &fp_seq, bool &ok) {
+    const Segment sg{0, seg_lo, seg_hi, 0};
     const int warps = blockDim.x >> 5;
-    const int per = warps - 1;  // tiles per chunk: one per consumer warp
+    constexpr int kTpw = (THREADS == 1024) ? 1 : 2;  // tiles per consumer warp and chunk
+    const int per = (warps - 1) * kTpw;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int d = P.d;
     const bool use_fp = P.pad != 0;
@@ -301,7 +405,9 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
             long long col0, col1;
             chunk_cols(P, sg.lo, sg.hi, c, per, col0, col1);
             const long long e_tma = (((col1 - col0) * d * 4) & ~15ll) / 4;  // ints that came by TMA
-            const int tile = sg.lo + c * per + (warp - 1);
+#pragma unroll
+            for (int u = 0; u < kTpw; ++u) {
+            const int tile = sg.lo + c * per + u * (warps - 1) + (warp - 1);
             bool acc = false;
             if (ok && tile < sg.hi) {
                 const int base = tile * kTile;
@@ -330,15 +436,12 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
                             }
                         }
                     }
-                    if (inline_exact) {
-                        unsigned long long omega;
-                        acc = exact_score<DMAX>(rows, d, P.r, a.alpha, a.mode, &omega);
-                        if (acc) apply_pair<DMAX>(P, j, rows, d, omega);
-                    }
+                    if (inline_exact) acc = score_inline<DMAX>(a, P, j, rows, d);
                 }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, acc);
             if (lane == 0 && bal) atomicAdd(S.acc, (unsigned long long)__popc(bal));
+            }
             __syncwarp();
             if (lane == 0) mbar_arrive(&S.empty[slot]);  // this warp is done with the stage
         }
@@ -349,30 +452,7 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
     if (a.stamps && blockIdx.x == 0 && threadIdx.x == 0 && g < kMaxStampIters)
         a.stamps[kSubBase + 3 * g + 1] = globaltimer();
 
-    // queued candidates: exact score, lane-parallel over the CTA.  The r
-    // gathers, x_hat_j and the in-slots flag go out in one round trip.
-    const int qn = min(*S.qn, a.queue_cap);
-    for (int b0 = warp * 32; b0 < qn; b0 += blockDim.x) {
-        const int idx = b0 + lane;
-        bool acc = false;
-        if (ok && idx < qn) {
-            const int32_t *e = S.queue + idx * (DMAX + 1);
-            const int j = e[0];
-            int32_t rows[DMAX];
-            unsigned long long v[DMAX];
-#pragma unroll
-            for (int t = 0; t < DMAX; ++t) rows[t] = e[1 + t];
-#pragma unroll
-            for (int t = 0; t < DMAX; ++t) v[t] = (t < d) ? value_bits(__ldcg(P.r + rows[t])) : 0ull;
-            const double xj = __ldcg(P.x_hat + j);
-            const uint8_t ins = __ldcg(P.in_slots + j);
-            unsigned long long omega;
-            acc = exact_score_values<DMAX>(v, d, a.alpha, a.mode, &omega);
-            if (acc) apply_pair_loaded<DMAX>(P, j, rows, d, omega, xj, ins);
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, acc);
-        if (lane == 0 && bal) atomicAdd(S.acc, (unsigned long long)__popc(bal));
-    }
+    score_queue<DMAX>(a, P, S, ok);
     // one global atomic per CTA and segment (all warps' counts summed on chip)
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -385,7 +465,7 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
 // One row of the residual phase.  The touched flag, the row's slot record,
 // y_i and the old r_i are independent loads issued together; only touched
 // rows then gather their contributors' x_hat_j.
-__device__ __forceinline__ long long residual_tile(const ProblemDev &P, int tile, int lane) {
+__device__ __noinline__ long long residual_tile(const ProblemDev &P, int tile, int lane) {
     const int i = tile * kTile + lane;
     long long delta = 0;
     if (i < P.m) {
@@ -417,7 +497,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
     S.fp = smem;
     S.stage = reinterpret_cast<char *>(smem + a.fp_cap);
     S.queue = reinterpret_cast<int32_t *>(S.stage + (size_t)a.stages * a.stage_bytes);
-    int8_t *s_status = reinterpret_cast<int8_t *>(S.queue + a.queue_cap * (DMAX + 1));
+    int8_t *s_status = reinterpret_cast<int8_t *>(
+        reinterpret_cast<char *>(S.queue) + ((a.queue_cap * (DMAX + 1) * 4 + 15) / 16) * 16);
+    long long *s_pref = reinterpret_cast<long long *>(
+        reinterpret_cast<char *>(s_status) + ((a.P + 15) / 16) * 16);  // a.P + 1 entries
     S.full = s_bars;
     S.empty = s_bars + kMaxStages;
     S.fp_bar = &s_bars[2 * kMaxStages];
@@ -438,16 +521,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
     __syncthreads();
 
     // ---- init: x_hat <- 0, r <- y (Alg. 2, first line) --------------------
-    const long long gtid = blockIdx.x * (long long)THREADS + threadIdx.x;
-    const long long gstride = (long long)gridDim.x * THREADS;
-    for (int p = 0; p < a.P; ++p) {
-        const ProblemDev &P = problem(a, p);
-        if (threadIdx.x == 0) s_sum = 0;
-        __syncthreads();
+    if (!a.probs) {
+        // one problem: grid-stride over its columns and rows
+        const ProblemDev &P = a.single;
+        const long long gtid = blockIdx.x * (long long)THREADS + threadIdx.x;
+        const long long gstride = (long long)gridDim.x * THREADS;
         for (long long j = gtid; j < P.n; j += gstride) {
             P.x_hat[j] = 0.0;
             P.in_slots[j] = 0;
         }
+        if (threadIdx.x == 0) s_sum = 0;
+        __syncthreads();
         long long nz = 0;
         for (long long i = gtid; i < P.m; i += gstride) {
             const double v = __ldg(P.y + i);
@@ -458,10 +542,49 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
             nz += (v != 0.0);
         }
         nz = warp_sum_ll(nz);
-        if (lane == 0 && nz) atomicAdd(reinterpret_cast<unsigned long long *>(&s_sum), (unsigned long long)nz);
+        if (lane == 0 && nz)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&s_sum), (unsigned long long)nz);
         __syncthreads();
         if (threadIdx.x == 0 && s_sum)
             atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0), (unsigned long long)s_sum);
+    } else {
+        build_partition<THREADS>(a, s_status, s_pref, kPartInitCols);
+        for_my_segments(a, s_status, s_pref, kPartInitCols,
+                        [&](int, const ProblemDev &P, int t0, int t1) {
+                            for (int t = t0 + warp; t < t1; t += kWarps) {
+                                const int j = t * kTile + lane;
+                                if (j < P.n) {
+                                    P.x_hat[j] = 0.0;
+                                    P.in_slots[j] = 0;
+                                }
+                            }
+                        });
+        build_partition<THREADS>(a, s_status, s_pref, kPartInitRows);
+        for_my_segments(a, s_status, s_pref, kPartInitRows,
+                        [&](int, const ProblemDev &P, int t0, int t1) {
+                            if (threadIdx.x == 0) s_sum = 0;
+                            __syncthreads();
+                            for (int t = t0 + warp; t < t1; t += kWarps) {
+                                const int i = t * kTile + lane;
+                                long long nz = 0;
+                                if (i < P.m) {
+                                    const double v = __ldg(P.y + i);
+                                    P.r[i] = v;
+                                    P.fp[i] = fingerprint(v);
+                                    P.touched[i] = 0;
+                                    P.slots[(size_t)i * kSlotRec] = 0;
+                                    nz = (v != 0.0);
+                                }
+                                nz = warp_sum_ll(nz);
+                                if (lane == 0 && nz)
+                                    atomicAdd(reinterpret_cast<unsigned long long *>(&s_sum),
+                                              (unsigned long long)nz);
+                            }
+                            __syncthreads();
+                            if (threadIdx.x == 0 && s_sum)
+                                atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0),
+                                          (unsigned long long)s_sum);
+                        });
     }
     if (!grid_barrier(a, bar++)) {
         fail_out(a);
@@ -489,14 +612,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
             for (int p = threadIdx.x; p < a.P; p += THREADS) problem(a, p).ctrl->acc[(g + 2) & 3] = 0;
 
         // ---- score + apply ------------------------------------------------
-        {
-            const SegList L = my_segments(a, true);
-            for (int s = 0; s < L.count; ++s) {
-                const Segment sg = L.segs ? L.segs[s] : L.one;
-                if (s_status[sg.prob] != kRunning || sg.hi <= sg.lo) continue;
-                score_segment<DMAX>(a, problem(a, sg.prob), sg, g, S, chunk_seq, fp_seq, ok);
-                if (!__syncthreads_and(ok)) break;
-            }
+        if (!a.probs) {
+            const long long tiles = (a.single.n + kTile - 1) / kTile;
+            const int t0 = (int)(tiles * blockIdx.x / gridDim.x);
+            const int t1 = (int)(tiles * (blockIdx.x + 1) / gridDim.x);
+            if (t1 > t0) score_segment<DMAX, THREADS>(a, a.single, t0, t1, g, S, chunk_seq, fp_seq, ok);
+        } else {
+            build_partition<THREADS>(a, s_status, s_pref, kPartScore);
+            for_my_segments(a, s_status, s_pref, kPartScore,
+                            [&](int, const ProblemDev &P, int t0, int t1) {
+                                if (!__syncthreads_and(ok)) return;
+                                score_segment<DMAX, THREADS>(a, P, t0, t1, g, S, chunk_seq, fp_seq, ok);
+                            });
         }
         if (!__syncthreads_and(ok)) {
             // a TMA wait ran out: give copies still in flight time to land, then leave
@@ -515,24 +642,26 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
         }
 
         // ---- residual + ||r||_0 ---------------------------------------------
-        {
-            const SegList L = my_segments(a, false);
-            for (int s = 0; s < L.count; ++s) {
-                const Segment sg = L.segs ? L.segs[s] : L.one;
-                if (s_status[sg.prob] != kRunning) continue;
-                const ProblemDev &P = problem(a, sg.prob);
-                if (threadIdx.x == 0) s_sum = 0;
-                __syncthreads();
-                for (int t = sg.lo + warp; t < sg.hi; t += kWarps) {
-                    const long long delta = residual_tile(P, t, lane);
-                    if (lane == 0 && delta)
-                        atomicAdd(reinterpret_cast<unsigned long long *>(&s_sum), (unsigned long long)delta);
-                }
-                __syncthreads();  // one global atomic per CTA and segment
-                if (threadIdx.x == 0 && s_sum)
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0),
-                              (unsigned long long)s_sum);
+        auto residual_segment = [&](const ProblemDev &P, int t0, int t1) {
+            if (threadIdx.x == 0) s_sum = 0;
+            __syncthreads();
+            for (int t = t0 + warp; t < t1; t += kWarps) {
+                const long long delta = residual_tile(P, t, lane);
+                if (lane == 0 && delta)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&s_sum), (unsigned long long)delta);
             }
+            __syncthreads();  // one global atomic per CTA and segment
+            if (threadIdx.x == 0 && s_sum)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0), (unsigned long long)s_sum);
+        };
+        if (!a.probs) {
+            const long long tiles = (a.single.m + kTile - 1) / kTile;
+            residual_segment(a.single, (int)(tiles * blockIdx.x / gridDim.x),
+                             (int)(tiles * (blockIdx.x + 1) / gridDim.x));
+        } else {
+            build_partition<THREADS>(a, s_status, s_pref, kPartRows);
+            for_my_segments(a, s_status, s_pref, kPartRows,
+                            [&](int, const ProblemDev &P, int t0, int t1) { residual_segment(P, t0, t1); });
         }
         if (!grid_barrier(a, bar++)) {
             fail_out(a);
@@ -579,20 +708,28 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
 // Host side
 // ---------------------------------------------------------------------------
 
-static int threads_for(int dmax) { return dmax <= 8 ? 1024 : 512; }
+// Schedules: (threads per CTA, tiles per consumer warp and chunk).
+//   1: 1024 threads, 1 tile  (d <= 8: at most 64 registers a thread)
+//   2:  512 threads, 2 tiles (any d: up to 128 registers a thread)
+static int schedule_for(int dmax, int requested) {
+    if (requested == 2 || dmax > 8) return 2;
+    return 1;  // measured faster for d <= 8 (more warps to hide latency)
+}
 
 typedef void (*engine_fn)(const EngineArgs);
 
-static engine_fn engine_kernel(int dmax) {
+#define CCS_ENGINE_CASES(T)                                                                   \
+    case 1: return k_engine<1, T>;   case 2: return k_engine<2, T>;                           \
+    case 3: return k_engine<3, T>;   case 4: return k_engine<4, T>;                           \
+    case 5: return k_engine<5, T>;   case 6: return k_engine<6, T>;                           \
+    case 7: return k_engine<7, T>;   case 8: return k_engine<8, T>;
+
+static engine_fn engine_kernel(int dmax, int schedule) {
+    if (schedule == 1) {
+        switch (dmax) { CCS_ENGINE_CASES(1024) default: return nullptr; }
+    }
     switch (dmax) {
-        case 1: return k_engine<1, 1024>;
-        case 2: return k_engine<2, 1024>;
-        case 3: return k_engine<3, 1024>;
-        case 4: return k_engine<4, 1024>;
-        case 5: return k_engine<5, 1024>;
-        case 6: return k_engine<6, 1024>;
-        case 7: return k_engine<7, 1024>;
-        case 8: return k_engine<8, 1024>;
+        CCS_ENGINE_CASES(512)
         case 9: return k_engine<9, 512>;
         case 10: return k_engine<10, 512>;
         case 11: return k_engine<11, 512>;
@@ -604,6 +741,7 @@ static engine_fn engine_kernel(int dmax) {
         default: return nullptr;
     }
 }
+#undef CCS_ENGINE_CASES
 
 static size_t stamps_bytes() {
     return align_up(sizeof(unsigned long long) * (kSubBase + 3 * kMaxStampIters), 256);
@@ -615,11 +753,7 @@ static size_t sync_bytes(int P) {
 
 size_t engine_header_bytes(int P) {
     size_t b = sync_bytes(P) + stamps_bytes();
-    if (P > 1) {
-        b += align_up(sizeof(ProblemDev) * (size_t)P, 256);
-        b += 2 * align_up(sizeof(int) * (kMaxBlocks + 1), 256);
-        b += 2 * align_up(sizeof(Segment) * (size_t)(kMaxBlocks + P), 256);
-    }
+    if (P > 1) b += align_up(sizeof(ProblemDev) * (size_t)P, 256);
     return b;
 }
 
@@ -683,39 +817,6 @@ static int blocks_per_sm(int dev, engine_fn fn, int threads, size_t smem) {
     return per_sm;
 }
 
-// Split P problems' tiles (weight w_p each) into G contiguous shares.
-static void partition(const std::vector<long long> &tiles, const std::vector<int> &weight, int G,
-                      std::vector<int> &ptr, std::vector<Segment> &segs) {
-    std::vector<std::vector<Segment>> per(G);
-    long long W = 0;
-    for (size_t p = 0; p < tiles.size(); ++p) W += tiles[p] * weight[p];
-    long long S = 0;  // weight before problem p
-    for (size_t p = 0; p < tiles.size(); ++p) {
-        const long long c = tiles[p], w = weight[p];
-        if (c == 0) continue;
-        auto first_tile = [&](long long b) -> long long {  // first tile with start*G >= b*W
-            long long num = b * W - S * G;
-            if (num <= 0) return 0;
-            long long t = (num + w * G - 1) / (w * G);
-            return std::min(t, c);
-        };
-        long long b0 = std::min<long long>(G - 1, (S * G) / std::max<long long>(W, 1));
-        long long b1 = std::min<long long>(G - 1, ((S + (c - 1) * w) * G) / std::max<long long>(W, 1));
-        for (long long b = b0; b <= b1; ++b) {
-            const long long lo = first_tile(b), hi = (b == G - 1) ? c : first_tile(b + 1);
-            if (hi > lo) per[b].push_back(Segment{(int)p, (int)lo, (int)hi, 0});
-        }
-        S += c * w;
-    }
-    ptr.assign(G + 1, 0);
-    segs.clear();
-    for (int b = 0; b < G; ++b) {
-        ptr[b] = (int)segs.size();
-        segs.insert(segs.end(), per[b].begin(), per[b].end());
-    }
-    ptr[G] = (int)segs.size();
-}
-
 // Launch the engine on P problems whose arrays are already carved out in
 // `pds` (ctrl pointers into the header of `ws`).  Fills out[0..P).
 int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *out, char *ws,
@@ -731,8 +832,10 @@ int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *
         set_last_error("csc_rows must be 16-byte aligned for the persistent engine");
         return CCS_EINVAL;
     }
-    engine_fn fn = engine_kernel(dmax);
-    const int threads = threads_for(dmax);
+    const int sched = schedule_for(dmax, prm.schedule);
+    engine_fn fn = engine_kernel(dmax, sched);
+    const int threads = sched == 1 ? 1024 : 512;
+    const int tpw = sched == 1 ? 1 : 2;  // kTpw of the kernel instance
     const int warps = threads / 32;
     int dev = 0;
     CCS_CUDA_TRY(cudaGetDevice(&dev));
@@ -741,9 +844,13 @@ int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *
         set_last_error("could not size the engine's shared memory");
         return CCS_ECUDA;
     }
-    const size_t stage_bytes = align_up((size_t)(warps - 1) * kTile * dmax * 4, 128);
+    const size_t stage_bytes = align_up((size_t)(warps - 1) * tpw * kTile * dmax * 4, 128);
     const size_t entry = (size_t)(dmax + 1) * 4;  // one queued candidate
-    const size_t status_bytes = align_up((size_t)P, 16);
+    const size_t status_bytes = align_up((size_t)P, 16) + sizeof(long long) * (size_t)(P + 1);
+    if (P > kMaxProblems) {
+        set_last_error("at most %d problems per launch (got %d)", kMaxProblems, P);
+        return CCS_EINVAL;
+    }
     const size_t fixed = status_bytes + 256 + kMinQueue * entry;
     if (fixed + 2 * stage_bytes > smem_limit) {
         set_last_error("too many problems in one launch (%d)", P);
@@ -761,9 +868,9 @@ int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *
     const int stages =
         (int)std::min<size_t>(kMaxStages, (smem_limit - fixed - fp_cap) / stage_bytes);
     const size_t left = smem_limit - fp_cap - (size_t)stages * stage_bytes - status_bytes - 256;
-    const int queue_cap = (int)std::min<size_t>(kQueueCap, left / entry);
-    const size_t smem = fp_cap + (size_t)stages * stage_bytes + (size_t)queue_cap * entry +
-                        status_bytes;
+    const int queue_cap = (int)std::min<size_t>(kQueueCap, (left - 16) / entry);
+    const size_t smem = fp_cap + (size_t)stages * stage_bytes +
+                        align_up((size_t)queue_cap * entry, 16) + status_bytes;
 
     const DeviceInfo di = device_info(dev);
     if (!di.coop) {
@@ -806,41 +913,9 @@ int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *
     } else {
         ProblemDev *d_probs = reinterpret_cast<ProblemDev *>(e);
         e += align_up(sizeof(ProblemDev) * (size_t)P, 256);
-        int *sptr = reinterpret_cast<int *>(e);
-        e += align_up(sizeof(int) * (kMaxBlocks + 1), 256);
-        int *rptr = reinterpret_cast<int *>(e);
-        e += align_up(sizeof(int) * (kMaxBlocks + 1), 256);
-        Segment *ssegs = reinterpret_cast<Segment *>(e);
-        e += align_up(sizeof(Segment) * (size_t)(kMaxBlocks + P), 256);
-        Segment *rsegs = reinterpret_cast<Segment *>(e);
-        std::vector<long long> ct(P), rt(P);
-        std::vector<int> cw(P), rw(P, 1);
-        for (int p = 0; p < P; ++p) {
-            ct[p] = (pds[p].n + kTile - 1) / kTile;
-            rt[p] = (pds[p].m + kTile - 1) / kTile;
-            cw[p] = pds[p].d;
-        }
-        std::vector<int> hsp, hrp;
-        std::vector<Segment> hss, hrs;
-        partition(ct, cw, G, hsp, hss);
-        partition(rt, rw, G, hrp, hrs);
         CCS_CUDA_TRY(cudaMemcpyAsync(d_probs, pds.data(), sizeof(ProblemDev) * P,
                                      cudaMemcpyHostToDevice, s));
-        CCS_CUDA_TRY(cudaMemcpyAsync(sptr, hsp.data(), sizeof(int) * (G + 1),
-                                     cudaMemcpyHostToDevice, s));
-        CCS_CUDA_TRY(cudaMemcpyAsync(rptr, hrp.data(), sizeof(int) * (G + 1),
-                                     cudaMemcpyHostToDevice, s));
-        if (!hss.empty())
-            CCS_CUDA_TRY(cudaMemcpyAsync(ssegs, hss.data(), sizeof(Segment) * hss.size(),
-                                         cudaMemcpyHostToDevice, s));
-        if (!hrs.empty())
-            CCS_CUDA_TRY(cudaMemcpyAsync(rsegs, hrs.data(), sizeof(Segment) * hrs.size(),
-                                         cudaMemcpyHostToDevice, s));
         a.probs = d_probs;
-        a.score_ptr = sptr;
-        a.score_segs = ssegs;
-        a.res_ptr = rptr;
-        a.res_segs = rsegs;
     }
 
     void *args[] = {&a};

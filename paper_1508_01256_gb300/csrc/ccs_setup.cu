@@ -314,7 +314,8 @@ void ccs_params_init(ccs_params *p) {
     p->engine = CCS_ENGINE_AUTO;
     p->watchdog_ms = 0;
     p->debug_flags = 0;
-    p->reserved[0] = p->reserved[1] = 0;
+    p->schedule = 0;
+    p->reserved = 0;
 }
 
 size_t ccs_workspace_size(int32_t op, int32_t n, int32_t m, int32_t d) {
