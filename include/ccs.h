@@ -246,6 +246,39 @@ CCS_API int ccs_decode_batch_async(const ccs_problem *probs, int32_t count,
                                    const ccs_params *p, ccs_result *out_dev,
                                    void *ws, size_t ws_bytes, ccs_stream_t stream);
 
+/*
+ * ccs_decode_parallel_l0_noalloc -- ccs_decode_parallel_l0 for callers that
+ * cannot allocate device memory when they decode (a memory budget that is
+ * already fully reserved, a real-time loop where an allocation and the
+ * synchronisation it may bring are not allowed, a host that only hands out
+ * pre-registered buffers).  The paper has no counterpart: this is a
+ * deployment variant of the same decode, with the same results.
+ *
+ * The caller passes the inputs and outputs as for ccs_decode_parallel_l0
+ * but no workspace: the scratch is one device array of
+ * ccs_noalloc_scratch_bytes() bytes (16 MiB) that the library keeps in every
+ * GPU that loads it, until the process exits.  Sizes whose workspace
+ * (ccs_workspace_size(CCS_OP_DECODE, n, m, d)) exceeds it are rejected with
+ * CCS_EINVAL; n = 2^20, m = 2^17, d = 7 fits.  The call allocates nothing:
+ * no cudaMalloc, no cudaFree, no allocating library routine.  Its first call
+ * on a device looks up that device's address of the array
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call on a device shares the one array, which keeps the last call's
+ * contents (the decode clears what must start at zero), so calls whose
+ * work overlaps on the GPU race: issue them one after another on one stream
+ * or otherwise order them.  Persistent engine only (CCS_ENGINE_HOST_LOOP is
+ * CCS_EINVAL).  Blocks until the decode has finished.
+ */
+CCS_API int ccs_decode_parallel_l0_noalloc(int32_t n, int32_t m, int32_t d,
+                                           const int32_t *csc_rows, const int64_t *csr_ptr,
+                                           const int32_t *csr_cols, const double *y,
+                                           double *x_hat, double *r, int64_t *r0_hist,
+                                           const ccs_params *p, ccs_result *out,
+                                           ccs_stream_t stream);
+
+/* Bytes of the static scratch behind ccs_decode_parallel_l0_noalloc. */
+CCS_API size_t ccs_noalloc_scratch_bytes(void);
+
 /* ---- measurement hooks ---------------------------------------------------
  * Kernel timing for benchmarks: between ccs_profile_begin() and
  * ccs_profile_end() the library brackets each of its kernel launches with

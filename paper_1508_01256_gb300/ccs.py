@@ -106,6 +106,12 @@ def lib() -> ctypes.CDLL:
                                                    ctypes.POINTER(Params), P, P, sz, P]
         l.ccs_decode_batch_async.argtypes = [ctypes.POINTER(Problem), i32, ctypes.POINTER(Params),
                                              P, P, sz, P]
+        l.ccs_decode_parallel_l0_noalloc.argtypes = [i32, i32, i32, P, P, P, P, P, P, P,
+                                                     ctypes.POINTER(Params),
+                                                     ctypes.POINTER(Result), P]
+        l.ccs_decode_parallel_l0_noalloc.restype = ctypes.c_int
+        l.ccs_noalloc_scratch_bytes.argtypes = []
+        l.ccs_noalloc_scratch_bytes.restype = sz
         l.ccs_profile_begin.argtypes = []
         l.ccs_profile_end.argtypes = [ctypes.POINTER(KernelTime)]
         l.ccs_profile_phases.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
@@ -227,6 +233,22 @@ def result_buffer(count: int, device="cuda"):
 def results_from_device(buf, count: int) -> list[Result]:
     raw = bytes(buf[:count * RESULT_BYTES].cpu().numpy().tobytes())
     return [Result.from_buffer_copy(raw, i * RESULT_BYTES) for i in range(count)]
+
+
+def ccs_decode_parallel_l0_noalloc(n, m, d, csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist,
+                                   p: Params | None, stream=None) -> Result:
+    """The decode without a caller workspace (library-held static scratch)."""
+    out = Result()
+    rc = lib().ccs_decode_parallel_l0_noalloc(
+        n, m, d, _ptr(csc_rows), _ptr(csr_ptr), _ptr(csr_cols), _ptr(y), _ptr(x_hat), _ptr(r),
+        _ptr(r0_hist), ctypes.byref(p) if p is not None else None, ctypes.byref(out),
+        _stream(stream))
+    _check(rc, "ccs_decode_parallel_l0_noalloc")
+    return out
+
+
+def ccs_noalloc_scratch_bytes() -> int:
+    return int(lib().ccs_noalloc_scratch_bytes())
 
 
 def ccs_decode_batch(probs, p: Params | None, ws, stream=None) -> list[Result]:

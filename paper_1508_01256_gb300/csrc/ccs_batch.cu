@@ -83,7 +83,7 @@ static int decode_batch_impl(const ccs_problem *probs, int32_t count, const ccs_
         }
         return CCS_OK;
     }
-    return engine_run(pds, p, out, hdr, s, dev_out);
+    return engine_run(pds.data(), count, p, out, hdr, s, dev_out);
 }
 
 extern "C" int ccs_decode_batch(const ccs_problem *probs, int32_t count, const ccs_params *params,

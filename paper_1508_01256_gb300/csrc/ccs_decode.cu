@@ -267,8 +267,7 @@ extern "C" int ccs_decode_parallel_l0(int32_t n, int32_t m, int32_t d, const int
     if (rc) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (p.engine == CCS_ENGINE_HOST_LOOP) return decode_host_loop(P, p, out, s);
-    std::vector<ProblemDev> one(1, P);
-    return engine_run(one, p, out, static_cast<char *>(ws), s);
+    return engine_run(&P, 1, p, out, static_cast<char *>(ws), s);
 }
 
 extern "C" int ccs_decode_parallel_l0_async(int32_t n, int32_t m, int32_t d,
@@ -286,8 +285,7 @@ extern "C" int ccs_decode_parallel_l0_async(int32_t n, int32_t m, int32_t d,
         set_last_error("ccs_decode_parallel_l0_async: the host-driven engine cannot run asynchronously");
         return CCS_EINVAL;
     }
-    std::vector<ProblemDev> one(1, P);
     ccs_result unused;
-    return engine_run(one, p, &unused, static_cast<char *>(ws),
+    return engine_run(&P, 1, p, &unused, static_cast<char *>(ws),
                       reinterpret_cast<cudaStream_t>(stream), out_dev);
 }

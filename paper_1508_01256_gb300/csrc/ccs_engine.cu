@@ -30,7 +30,6 @@
 // land, and returns; the host reports CCS_ETIMEOUT.
 #include <algorithm>
 #include <cstring>
-#include <map>
 #include <mutex>
 #include <tuple>
 #include <vector>
@@ -761,21 +760,26 @@ DecodeCtrl *header_ctrl(char *ws, int p) {
     return reinterpret_cast<DecodeCtrl *>(ws + sizeof(EngineSync)) + p;
 }
 
+// Launch-setting caches: fixed tables (no heap allocation), filled on first
+// use per device and kernel.
 struct DeviceInfo {
     int sms = 0;
     int coop = 0;
+    bool valid = false;
 };
+
+constexpr int kMaxDevices = 64;
 
 static DeviceInfo device_info(int dev) {
     static std::mutex mu;
-    static std::map<int, DeviceInfo> cache;
+    static DeviceInfo cache[kMaxDevices];
     std::lock_guard<std::mutex> lk(mu);
-    auto it = cache.find(dev);
-    if (it != cache.end()) return it->second;
     DeviceInfo di;
+    if (dev >= 0 && dev < kMaxDevices && cache[dev].valid) return cache[dev];
     cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&di.coop, cudaDevAttrCooperativeLaunch, dev);
-    cache[dev] = di;
+    di.valid = true;
+    if (dev >= 0 && dev < kMaxDevices) cache[dev] = di;
     return di;
 }
 
@@ -784,12 +788,17 @@ static DeviceInfo device_info(int dev) {
 // The kernel's attribute is raised to it once, so every later launch of any
 // size up to it is allowed.  Returns 0 on failure.
 static size_t max_dynamic_smem(int dev, engine_fn fn) {
+    struct Entry {
+        int dev;
+        engine_fn fn;
+        size_t lim;
+    };
     static std::mutex mu;
-    static std::map<std::pair<int, void *>, size_t> cache;
+    static Entry cache[256];
+    static int used = 0;
     std::lock_guard<std::mutex> lk(mu);
-    auto key = std::make_pair(dev, (void *)fn);
-    auto it = cache.find(key);
-    if (it != cache.end()) return it->second;
+    for (int e = 0; e < used; ++e)
+        if (cache[e].dev == dev && cache[e].fn == fn) return cache[e].lim;
     int optin = 0;
     cudaFuncAttributes fa;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
@@ -798,35 +807,40 @@ static size_t max_dynamic_smem(int dev, engine_fn fn) {
     const size_t lim = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim) != cudaSuccess)
         return 0;
-    cache[key] = lim;
+    if (used < 256) cache[used++] = Entry{dev, fn, lim};
     return lim;
 }
 
 // Resident CTAs per SM for (kernel, dynamic smem), cached.
 static int blocks_per_sm(int dev, engine_fn fn, int threads, size_t smem) {
+    struct Entry {
+        int dev;
+        engine_fn fn;
+        size_t smem;
+        int per_sm;
+    };
     static std::mutex mu;
-    static std::map<std::tuple<int, void *, size_t>, int> cache;
+    static Entry cache[1024];
+    static int used = 0;
     std::lock_guard<std::mutex> lk(mu);
-    auto key = std::make_tuple(dev, (void *)fn, smem);
-    auto it = cache.find(key);
-    if (it != cache.end()) return it->second;
+    for (int e = 0; e < used; ++e)
+        if (cache[e].dev == dev && cache[e].fn == fn && cache[e].smem == smem) return cache[e].per_sm;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess)
         return -1;
-    cache[key] = per_sm;
+    if (used < 1024) cache[used++] = Entry{dev, fn, smem, per_sm};
     return per_sm;
 }
 
 // Launch the engine on P problems whose arrays are already carved out in
 // `pds` (ctrl pointers into the header of `ws`).  Fills out[0..P).
-int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *out, char *ws,
+int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, char *ws,
                cudaStream_t s, ccs_result *dev_out) {
-    const int P = (int)pds.size();
     int dmax = 1;
     bool aligned = true;
-    for (auto &pd : pds) {
-        dmax = std::max(dmax, pd.d);
-        aligned &= (reinterpret_cast<uintptr_t>(pd.csc_rows) & 15u) == 0;
+    for (int p = 0; p < P; ++p) {
+        dmax = std::max(dmax, pds[p].d);
+        aligned &= (reinterpret_cast<uintptr_t>(pds[p].csc_rows) & 15u) == 0;
     }
     if (!aligned) {
         set_last_error("csc_rows must be 16-byte aligned for the persistent engine");
@@ -859,7 +873,8 @@ int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *
     // fingerprints in shared memory when they leave room for >= 2 CSC stages
     const size_t fp_budget = smem_limit - fixed - 2 * stage_bytes;
     size_t fp_cap = 0;
-    for (auto &pd : pds) {
+    for (int p = 0; p < P; ++p) {
+        ProblemDev &pd = pds[p];
         const size_t need = align_up((size_t)pd.m, 16);
         pd.pad = need <= fp_budget ? 1 : 0;
         if (pd.pad) fp_cap = std::max(fp_cap, need);
@@ -913,7 +928,7 @@ int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *
     } else {
         ProblemDev *d_probs = reinterpret_cast<ProblemDev *>(e);
         e += align_up(sizeof(ProblemDev) * (size_t)P, 256);
-        CCS_CUDA_TRY(cudaMemcpyAsync(d_probs, pds.data(), sizeof(ProblemDev) * P,
+        CCS_CUDA_TRY(cudaMemcpyAsync(d_probs, pds, sizeof(ProblemDev) * P,
                                      cudaMemcpyHostToDevice, s));
         a.probs = d_probs;
     }
@@ -925,9 +940,17 @@ int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *
     count_launches(1);
     if (dev_out) return CCS_OK;  // asynchronous: the kernel writes the results
 
-    // results: one copy of the sync word and every control block
-    std::vector<char> hdr(sizeof(EngineSync) + sizeof(DecodeCtrl) * (size_t)P);
-    CCS_CUDA_TRY(cudaMemcpyAsync(hdr.data(), ws, hdr.size(), cudaMemcpyDeviceToHost, s));
+    // results: one copy of the sync word and every control block (a stack
+    // buffer for small launches, so single decodes allocate nothing)
+    const size_t hdr_bytes = sizeof(EngineSync) + sizeof(DecodeCtrl) * (size_t)P;
+    alignas(64) char hdr_small[sizeof(EngineSync) + sizeof(DecodeCtrl) * 8];
+    std::vector<char> hdr_big;
+    char *hdr = hdr_small;
+    if (P > 8) {
+        hdr_big.resize(hdr_bytes);
+        hdr = hdr_big.data();
+    }
+    CCS_CUDA_TRY(cudaMemcpyAsync(hdr, ws, hdr_bytes, cudaMemcpyDeviceToHost, s));
     std::vector<unsigned long long> hst;
     if (a.stamps) {
         hst.resize(kSubBase + 3 * kMaxStampIters);
@@ -936,13 +959,12 @@ int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *
     }
     CCS_CUDA_TRY(cudaStreamSynchronize(s));
     EngineSync hs;
-    std::memcpy(&hs, hdr.data(), sizeof(hs));
+    std::memcpy(&hs, hdr, sizeof(hs));
     const int herr = hs.error;
     int max_it = 0;
     for (int p = 0; p < P; ++p) {
         DecodeCtrl hc;
-        std::memcpy(&hc, hdr.data() + sizeof(EngineSync) + sizeof(DecodeCtrl) * (size_t)p,
-                    sizeof(hc));
+        std::memcpy(&hc, hdr + sizeof(EngineSync) + sizeof(DecodeCtrl) * (size_t)p, sizeof(hc));
         out[p].status = hc.status;
         out[p].iterations = hc.iteration;
         out[p].r0_final = hc.r0;

@@ -139,7 +139,7 @@ int decode_host_loop(const ProblemDev &P, const ccs_params &p, ccs_result *out, 
 // engine_header_bytes(P) bytes: EngineSync, P DecodeCtrl, engine scratch.
 size_t engine_header_bytes(int P);
 DecodeCtrl *header_ctrl(char *ws, int p);
-int engine_run(std::vector<ProblemDev> &pds, const ccs_params &prm, ccs_result *out, char *ws,
+int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, char *ws,
                cudaStream_t s, ccs_result *dev_out = nullptr);
 int check_params(const ccs_params *p, int d);
 
