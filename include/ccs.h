@@ -103,7 +103,8 @@ typedef struct {
                              choice (1 when d <= 8, else 2); 1 = 1024
                              threads a CTA, one 32-column tile per warp and
                              chunk (d <= 8 only); 2 = 512 threads, two
-                             tiles per warp and chunk                       */
+                             tiles per warp and chunk; 3 = 768 threads, one
+                             tile per warp and chunk (d <= 8 only)          */
     int32_t reserved;     /* must be zero                                     */
 } ccs_params;
 

@@ -163,7 +163,7 @@ int check_params(const ccs_params *p, int d) {
         set_last_error("unknown engine %d", p->engine);
         return CCS_EINVAL;
     }
-    if (p->watchdog_ms < 0 || p->reserved || p->schedule < 0 || p->schedule > 2) {
+    if (p->watchdog_ms < 0 || p->reserved || p->schedule < 0 || p->schedule > 3) {
         set_last_error("bad watchdog_ms, schedule or nonzero reserved field");
         return CCS_EINVAL;
     }

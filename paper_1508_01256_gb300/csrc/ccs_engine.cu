@@ -125,11 +125,27 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// try_wait that may suspend the thread for up to `hint_ns` while the phase
+// is incomplete (it returns as soon as the phase completes), so waiting
+// warps do not spin through issue slots.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity,
+                                                    uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait on an mbarrier phase.  On time-out marks the launch failed.
 __device__ __forceinline__ bool mbar_wait(const EngineArgs &a, uint64_t *bar, uint32_t parity) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
-    while (!mbar_try_wait(bar, parity)) {
+    while (!mbar_try_wait_sleep(bar, parity, 20000u)) {
         if (globaltimer() - t0 > (unsigned long long)a.watchdog_ns) {
             atomicOr(&a.sync->error, kErrWatchdog);
             return false;
@@ -305,10 +321,14 @@ __device__ __forceinline__ void issue_chunk(const EngineArgs &a, const ProblemDe
 }
 
 // Exact score and apply of one column inside the stream (problems without
-// shared-memory fingerprints, or a full queue).
+// shared-memory fingerprints, or a full queue); the rows are read again from
+// global memory, so the stream loop keeps no copy of them.
 template <int DMAX>
-__device__ __forceinline__ bool score_inline(const EngineArgs &a, const ProblemDev &P, int j,
-                                          const int32_t (&rows)[DMAX], int d) {
+__device__ __forceinline__ bool score_inline(const EngineArgs &a, const ProblemDev &P, int j) {
+    const int d = P.d;
+    int32_t rows[DMAX];
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t) rows[t] = (t < d) ? __ldg(P.csc_rows + (size_t)j * d + t) : 0;
     unsigned long long omega;
     const bool acc = exact_score<DMAX>(rows, d, P.r, a.alpha, a.mode, &omega);
     if (acc) apply_pair<DMAX>(P, j, rows, d, omega);
@@ -318,16 +338,16 @@ __device__ __forceinline__ bool score_inline(const EngineArgs &a, const ProblemD
 // Queued candidates: exact score, lane-parallel over the CTA.  The r
 // gathers, x_hat_j and the in-slots flag go out in one round trip.
 template <int DMAX>
-__device__ __forceinline__ void score_queue(const EngineArgs &a, const ProblemDev &P, ScoreSmem &S,
-                                         bool ok) {
+__device__ __forceinline__ void score_queue(const EngineArgs &a, const ProblemDev &P,
+                                         const int32_t *queue, int qn,
+                                         unsigned long long *acc_smem, bool ok) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int d = P.d;
-    const int qn = min(*S.qn, a.queue_cap);
     for (int b0 = warp * 32; b0 < qn; b0 += blockDim.x) {
         const int idx = b0 + lane;
         bool acc = false;
         if (ok && idx < qn) {
-            const int32_t *e = S.queue + idx * (DMAX + 1);
+            const int32_t *e = queue + idx * (DMAX + 1);
             const int j = e[0];
             int32_t rows[DMAX];
             unsigned long long v[DMAX];
@@ -342,7 +362,7 @@ __device__ __forceinline__ void score_queue(const EngineArgs &a, const ProblemDe
             if (acc) apply_pair_loaded<DMAX>(P, j, rows, d, omega, xj, ins);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, acc);
-        if (lane == 0 && bal) atomicAdd(S.acc, (unsigned long long)__popc(bal));
+        if (lane == 0 && bal) atomicAdd(acc_smem, (unsigned long long)__popc(bal));
     }
 }
 
@@ -357,7 +377,7 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
                                               unsigned &chunk_seq, unsigned &fp_seq, bool &ok) {
     const Segment sg{0, seg_lo, seg_hi, 0};
     const int warps = blockDim.x >> 5;
-    constexpr int kTpw = (THREADS == 1024) ? 1 : 2;  // tiles per consumer warp and chunk
+    constexpr int kTpw = (THREADS == 512) ? 2 : 1;  // tiles per consumer warp and chunk
     const int per = (warps - 1) * kTpw;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int d = P.d;
@@ -403,7 +423,10 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
                 reinterpret_cast<const int32_t *>(S.stage + (size_t)slot * a.stage_bytes);
             long long col0, col1;
             chunk_cols(P, sg.lo, sg.hi, c, per, col0, col1);
-            const long long e_tma = (((col1 - col0) * d * 4) & ~15ll) / 4;  // ints that came by TMA
+            // ints of this chunk that came by TMA; only a problem's last chunk
+            // can end with up to 3 ints that did not
+            const long long e_tma = (((col1 - col0) * d * 4) & ~15ll) / 4;
+            const bool tail = e_tma != (col1 - col0) * d;
 #pragma unroll
             for (int u = 0; u < kTpw; ++u) {
             const int tile = sg.lo + c * per + u * (warps - 1) + (warp - 1);
@@ -415,11 +438,16 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
                     const int j = base + lane;
                     const long long e0 = (long long)(j - col0) * d;  // first int of column j
                     int32_t rows[DMAX];
+                    if (!tail) {
 #pragma unroll
-                    for (int t = 0; t < DMAX; ++t)
-                        rows[t] = (t < d) ? ((e0 + t < e_tma) ? stage[e0 + t]
-                                                              : __ldg(P.csc_rows + (size_t)j * d + t))
-                                          : 0;
+                        for (int t = 0; t < DMAX; ++t) rows[t] = (t < d) ? stage[e0 + t] : 0;
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < DMAX; ++t)
+                            rows[t] = (t < d) ? ((e0 + t < e_tma) ? stage[e0 + t]
+                                                                  : __ldg(P.csc_rows + (size_t)j * d + t))
+                                              : 0;
+                    }
                     bool inline_exact = true;
                     if (use_fp) {
                         inline_exact = false;
@@ -435,7 +463,7 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
                             }
                         }
                     }
-                    if (inline_exact) acc = score_inline<DMAX>(a, P, j, rows, d);
+                    if (inline_exact) acc = score_inline<DMAX>(a, P, j);
                 }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, acc);
@@ -451,7 +479,7 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
     if (a.stamps && blockIdx.x == 0 && threadIdx.x == 0 && g < kMaxStampIters)
         a.stamps[kSubBase + 3 * g + 1] = globaltimer();
 
-    score_queue<DMAX>(a, P, S, ok);
+    score_queue<DMAX>(a, P, S.queue, min(*S.qn, a.queue_cap), S.acc, ok);
     // one global atomic per CTA and segment (all warps' counts summed on chip)
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -710,9 +738,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
 // Schedules: (threads per CTA, tiles per consumer warp and chunk).
 //   1: 1024 threads, 1 tile  (d <= 8: at most 64 registers a thread)
 //   2:  512 threads, 2 tiles (any d: up to 128 registers a thread)
+//   3:  768 threads, 1 tile  (d <= 8: up to 85 registers a thread)
 static int schedule_for(int dmax, int requested) {
     if (requested == 2 || dmax > 8) return 2;
-    return 1;  // measured faster for d <= 8 (more warps to hide latency)
+    if (requested == 3) return 3;
+    return 1;  // measured fastest for d <= 8
 }
 
 typedef void (*engine_fn)(const EngineArgs);
@@ -726,6 +756,9 @@ typedef void (*engine_fn)(const EngineArgs);
 static engine_fn engine_kernel(int dmax, int schedule) {
     if (schedule == 1) {
         switch (dmax) { CCS_ENGINE_CASES(1024) default: return nullptr; }
+    }
+    if (schedule == 3) {
+        switch (dmax) { CCS_ENGINE_CASES(768) default: return nullptr; }
     }
     switch (dmax) {
         CCS_ENGINE_CASES(512)
@@ -848,8 +881,8 @@ int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, c
     }
     const int sched = schedule_for(dmax, prm.schedule);
     engine_fn fn = engine_kernel(dmax, sched);
-    const int threads = sched == 1 ? 1024 : 512;
-    const int tpw = sched == 1 ? 1 : 2;  // kTpw of the kernel instance
+    const int threads = sched == 1 ? 1024 : (sched == 3 ? 768 : 512);
+    const int tpw = sched == 2 ? 2 : 1;  // kTpw of the kernel instance
     const int warps = threads / 32;
     int dev = 0;
     CCS_CUDA_TRY(cudaGetDevice(&dev));
