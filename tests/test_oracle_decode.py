@@ -4,7 +4,7 @@ The theorem-regime cases use the point-line incidence matrix of the affine
 plane AG(2, q) (q prime): its q^2 + q lines are the columns, its q^2 points
 the rows, d = q, and two columns share at most one row.  For those graphs the
 expansion parameter eps of Def. 2 is found by brute force over all column
-sets of size <= k, and Theorem 1 (with Lemmas 3-5 and Eq. (37)) then fixes
+sets of size <= k, and Theorem 1 (with Lemmas 1-6 and Eq. (37)) then fixes
 what the decoder must do: accept only exact values x_j at the right j,
 shrink the support of x - x_hat by the factor of Eq. (37) every iteration,
 and end with x_hat = x, which brute force over all supports of size <= k
