@@ -247,6 +247,67 @@ CCS_API int ccs_decode_batch_async(const ccs_problem *probs, int32_t count,
                                    const ccs_params *p, ccs_result *out_dev,
                                    void *ws, size_t ws_bytes, ccs_stream_t stream);
 
+/* ---- serving: continuous batching -----------------------------------------
+ *
+ * A decode server with one worker thread.  Requests (ccs_problem: device
+ * arrays owned by the caller, kept alive until their result is collected)
+ * are queued by ccs_server_submit.  The worker runs engine rounds: one
+ * persistent launch over every admitted request, at most iters_per_round
+ * iterations of Alg. 2, each request's decode state kept on the device
+ * between rounds.  After each round finished requests are retired and
+ * pending ones admitted, in arrival order, as long as their state fits the
+ * memory pool and a batch slot is free; so requests arriving while others
+ * run join them on the GPU.  Every result is bit-identical to
+ * ccs_decode_parallel_l0 on the same request.  Not in the paper: a serving
+ * layer over its decoder.
+ */
+typedef struct ccs_server ccs_server;
+
+typedef struct {
+    void *pool;               /* caller-owned device memory the server carves
+                                 request state and its launch header from    */
+    size_t pool_bytes;        /* its size: the HBM budget for request state  */
+    int32_t max_batch;        /* most requests in one round, 1..4096         */
+    int32_t iters_per_round;  /* iterations per round, >= 1                  */
+    ccs_params params;        /* decode parameters of every request          */
+} ccs_server_config;
+
+typedef struct {
+    ccs_result result;        /* as ccs_decode_parallel_l0 reports it        */
+    double submit_s, admit_s, done_s;  /* steady-clock seconds (one origin
+                                 per process): queued, admitted, finished    */
+    int32_t rounds;           /* engine rounds the request took part in      */
+    int32_t reserved;
+} ccs_ticket_info;
+
+typedef struct {
+    int64_t submitted, admitted, completed, rounds;
+    int64_t peak_inflight;    /* most requests in one round                  */
+    int64_t peak_bytes;       /* most pool bytes in use by request state     */
+    int64_t bytes_in_use, pending, inflight;
+    int32_t error;            /* first CCS_E* a round returned, else CCS_OK  */
+    int32_t reserved;
+} ccs_server_stats;
+
+/* Starts the worker on the current device; work goes to `stream`.
+ * CCS_EINVAL for a bad configuration, CCS_EBUDGET if the pool cannot even
+ * hold the launch header. */
+CCS_API int ccs_server_create(const ccs_server_config *cfg, ccs_stream_t stream,
+                              ccs_server **out);
+/* Queues a request; *ticket identifies it.  CCS_EBUDGET if its state can
+ * never fit the pool, CCS_EINVAL for bad sizes or arrays. */
+CCS_API int ccs_server_submit(ccs_server *s, const ccs_problem *req, int64_t *ticket);
+/* CCS_OK and *info once the request has finished (the ticket is then
+ * released); CCS_EBUSY while it is pending or running. */
+CCS_API int ccs_server_poll(ccs_server *s, int64_t ticket, ccs_ticket_info *info);
+/* As ccs_server_poll, waiting up to timeout_ms for the result. */
+CCS_API int ccs_server_wait(ccs_server *s, int64_t ticket, ccs_ticket_info *info,
+                            int32_t timeout_ms);
+CCS_API int ccs_server_stats_get(ccs_server *s, ccs_server_stats *out);
+/* Finishes every queued request, stops the worker, frees the handle.
+ * Returns the first error a round reported, else CCS_OK. */
+CCS_API int ccs_server_destroy(ccs_server *s);
+
 /*
  * ccs_decode_parallel_l0_noalloc -- ccs_decode_parallel_l0 for callers that
  * cannot allocate device memory when they decode (a memory budget that is

@@ -59,6 +59,25 @@ class Problem(ctypes.Structure):
                 ("r0_hist", ctypes.c_void_p)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("pool", ctypes.c_void_p), ("pool_bytes", ctypes.c_size_t),
+                ("max_batch", ctypes.c_int32), ("iters_per_round", ctypes.c_int32),
+                ("params", Params)]
+
+
+class TicketInfo(ctypes.Structure):
+    _fields_ = [("result", Result), ("submit_s", ctypes.c_double),
+                ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double),
+                ("rounds", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "admitted", "completed", "rounds",
+                                              "peak_inflight", "peak_bytes", "bytes_in_use",
+                                              "pending", "inflight")] + \
+               [("error", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -112,6 +131,15 @@ def lib() -> ctypes.CDLL:
         l.ccs_decode_parallel_l0_noalloc.restype = ctypes.c_int
         l.ccs_noalloc_scratch_bytes.argtypes = []
         l.ccs_noalloc_scratch_bytes.restype = sz
+        l.ccs_server_create.argtypes = [ctypes.POINTER(ServerConfig), P, ctypes.POINTER(P)]
+        l.ccs_server_submit.argtypes = [P, ctypes.POINTER(Problem), ctypes.POINTER(i64)]
+        l.ccs_server_poll.argtypes = [P, i64, ctypes.POINTER(TicketInfo)]
+        l.ccs_server_wait.argtypes = [P, i64, ctypes.POINTER(TicketInfo), i32]
+        l.ccs_server_stats_get.argtypes = [P, ctypes.POINTER(ServerStats)]
+        l.ccs_server_destroy.argtypes = [P]
+        for name in ("ccs_server_create", "ccs_server_submit", "ccs_server_poll",
+                     "ccs_server_wait", "ccs_server_stats_get", "ccs_server_destroy"):
+            getattr(l, name).restype = ctypes.c_int
         l.ccs_profile_begin.argtypes = []
         l.ccs_profile_end.argtypes = [ctypes.POINTER(KernelTime)]
         l.ccs_profile_phases.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
@@ -381,3 +409,101 @@ def decode_batch(items, alpha=2, max_iter=100, score_mode=SCORE_L0_DECREASE,
                                    iterations=rr.iterations, r0_final=rr.r0_final,
                                    error=rr.error))
     return result
+
+
+# ---- serving -------------------------------------------------------------------
+
+class Server:
+    """Continuous-batching decode server (ccs_server_* in include/ccs.h).
+
+    `pool_bytes` of device memory (a torch tensor held here) is the budget
+    for request state.  Requests are (csc_rows, csr_ptr, csr_cols, y, x_hat,
+    r[, r0_hist]) device tensors that must stay alive until collected."""
+
+    def __init__(self, pool_bytes: int, max_batch: int = 512, iters_per_round: int = 2,
+                 alpha=2, max_iter=100, score_mode=SCORE_L0_DECREASE, device="cuda",
+                 stream=None):
+        import torch
+        self.pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device=device)
+        cfg = ServerConfig(self.pool.data_ptr(), int(pool_bytes), max_batch, iters_per_round,
+                           params(alpha, max_iter, score_mode))
+        self._h = ctypes.c_void_p()
+        self._stream = torch.cuda.Stream(device=device) if stream is None else stream
+        _check(lib().ccs_server_create(ctypes.byref(cfg), self._stream.cuda_stream,
+                                       ctypes.byref(self._h)), "ccs_server_create")
+        self._keep = {}
+
+    def submit(self, csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist=None) -> int:
+        pb = problem(csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist)
+        t = ctypes.c_int64()
+        _check(lib().ccs_server_submit(self._h, ctypes.byref(pb), ctypes.byref(t)),
+               "ccs_server_submit")
+        self._keep[t.value] = (csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist)
+        return t.value
+
+    def poll(self, ticket: int):
+        info = TicketInfo()
+        rc = lib().ccs_server_poll(self._h, ticket, ctypes.byref(info))
+        if rc == CCS_EBUSY:
+            return None
+        _check(rc, "ccs_server_poll")
+        self._keep.pop(ticket, None)
+        return info
+
+    def wait(self, ticket: int, timeout_ms: int = 60000):
+        info = TicketInfo()
+        rc = lib().ccs_server_wait(self._h, ticket, ctypes.byref(info), timeout_ms)
+        if rc == CCS_EBUSY:
+            return None
+        _check(rc, "ccs_server_wait")
+        self._keep.pop(ticket, None)
+        return info
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().ccs_server_stats_get(self._h, ctypes.byref(st)), "ccs_server_stats_get")
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_ if f != "reserved"}
+
+    def close(self):
+        if self._h:
+            rc = lib().ccs_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            _check(rc, "ccs_server_destroy")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def serve_poisson(server: Server, requests, arrivals_s, timeout_ms: int = 120000):
+    """Submit requests[i] at time arrivals_s[i] (seconds from now) and collect
+    every result.  Returns a list of TicketInfo in submission order."""
+    import time
+    tickets, infos = [], [None] * len(requests)
+    done = threading.Event()
+
+    def collect():
+        i = 0
+        while i < len(requests):
+            if i >= len(tickets):
+                time.sleep(0.0001)
+                continue
+            info = server.wait(tickets[i], timeout_ms)
+            if info is None:
+                raise RuntimeError(f"request {i} not finished within {timeout_ms} ms")
+            infos[i] = info
+            i += 1
+        done.set()
+
+    th = threading.Thread(target=collect, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    for req, at in zip(requests, arrivals_s):
+        delay = t0 + at - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(server.submit(*req))
+    th.join()
+    return infos

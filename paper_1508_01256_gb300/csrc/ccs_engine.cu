@@ -67,6 +67,8 @@ struct EngineArgs {
     long long watchdog_ns;
     int debug_flags;
     ccs_result *dev_out;        // per-problem results in device memory (or null)
+    int resume;                 // control blocks persist; only kPdFresh problems initialise
+    int iter_budget;            // iterations this launch may run
 };
 
 // ---- device helpers --------------------------------------------------------
@@ -215,6 +217,15 @@ __device__ __forceinline__ long long part_weight(const ProblemDev &P, int kind) 
     return kind == kPartScore ? P.d : 1;
 }
 
+// Does problem P take part in a partition of this kind?  Iteration phases:
+// the running problems.  Init: every problem, or in resume mode the fresh
+// ones only.
+__device__ __forceinline__ bool part_on(const EngineArgs &a, const ProblemDev &P, int8_t status,
+                                        int kind) {
+    if (kind >= kPartInitCols) return !a.resume || (P.flags & kPdFresh);
+    return status == kRunning;
+}
+
 // pref[0..P]: exclusive prefix of the problems' weights (0 for problems
 // that are not running, except in the init kinds).  Block-wide.
 template <int THREADS>
@@ -228,11 +239,8 @@ __device__ __noinline__ void build_partition(const EngineArgs &a, const int8_t *
     for (int q = 0; q < per; ++q) {
         const int p = p0 + q;
         if (p < a.P) {
-            const bool on = kind >= kPartInitCols || status[p] == kRunning;
-            if (on) {
-                const ProblemDev &P = problem(a, p);
-                mine += part_tiles(P, kind) * part_weight(P, kind);
-            }
+            const ProblemDev &P = problem(a, p);
+            if (part_on(a, P, status[p], kind)) mine += part_tiles(P, kind) * part_weight(P, kind);
         }
     }
     long long inc = mine;
@@ -251,11 +259,8 @@ __device__ __noinline__ void build_partition(const EngineArgs &a, const int8_t *
         const int p = p0 + q;
         if (p < a.P) {
             pref[p] = run;
-            const bool on = kind >= kPartInitCols || status[p] == kRunning;
-            if (on) {
-                const ProblemDev &P = problem(a, p);
-                run += part_tiles(P, kind) * part_weight(P, kind);
-            }
+            const ProblemDev &P = problem(a, p);
+            if (part_on(a, P, status[p], kind)) run += part_tiles(P, kind) * part_weight(P, kind);
         }
     }
     if (threadIdx.x == THREADS - 1) pref[a.P] = run;
@@ -276,9 +281,8 @@ __device__ __forceinline__ void for_my_segments(const EngineArgs &a, const int8_
         else lo = mid + 1;
     }
     for (int p = lo; p < a.P && pref[p] < B1; ++p) {
-        const bool on = kind >= kPartInitCols || status[p] == kRunning;
-        if (!on) continue;
         const ProblemDev &P = problem(a, p);
+        if (!part_on(a, P, status[p], kind)) continue;
         const long long w = part_weight(P, kind), tiles = part_tiles(P, kind);
         const long long t0 = B0 > pref[p] ? (B0 - pref[p] + w - 1) / w : 0;
         const long long t1 = min(tiles, (B1 - pref[p] + w - 1) / w);
@@ -381,7 +385,7 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
     const int per = (warps - 1) * kTpw;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int d = P.d;
-    const bool use_fp = P.pad != 0;
+    const bool use_fp = (P.flags & kPdUseFp) != 0;
     const int tiles = sg.hi - sg.lo;
     const int nchunks = (tiles + per - 1) / per;
     unsigned long long *acc_slot = &P.ctrl->acc[g & 3];
@@ -528,6 +532,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
         reinterpret_cast<char *>(S.queue) + ((a.queue_cap * (DMAX + 1) * 4 + 15) / 16) * 16);
     long long *s_pref = reinterpret_cast<long long *>(
         reinterpret_cast<char *>(s_status) + ((a.P + 15) / 16) * 16);  // a.P + 1 entries
+    int *s_base = reinterpret_cast<int *>(s_pref + a.P + 1);          // a.P entries
     S.full = s_bars;
     S.empty = s_bars + kMaxStages;
     S.fp_bar = &s_bars[2 * kMaxStages];
@@ -545,6 +550,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
         mbar_init(S.fp_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    // resume mode: the accepted-count rings are per launch (the control
+    // blocks themselves persist); they are first used after the init barrier
+    if (a.resume && blockIdx.x == 0)
+        for (int p = threadIdx.x; p < a.P; p += THREADS)
+            for (int q = 0; q < 4; ++q) problem(a, p).ctrl->acc[q] = 0;
     __syncthreads();
 
     // ---- init: x_hat <- 0, r <- y (Alg. 2, first line) --------------------
@@ -619,9 +629,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
     }
     for (int p = threadIdx.x; p < a.P; p += THREADS) {
         const ProblemDev &P = problem(a, p);
+        if (a.resume && !(P.flags & kPdFresh)) {
+            // continues from an earlier launch
+            s_status[p] = (int8_t)__ldcg(&P.ctrl->status);
+            s_base[p] = __ldcg(&P.ctrl->iteration);
+            continue;
+        }
         const long long r0 = __ldcg(&P.ctrl->r0);
         const int st = (r0 == 0) ? CCS_CONVERGED : (a.max_iter == 0 ? CCS_MAX_ITER : kRunning);
         s_status[p] = (int8_t)st;
+        s_base[p] = 0;
         if (blockIdx.x == 0) {
             P.ctrl->status = st;
             P.ctrl->iteration = 0;
@@ -631,7 +648,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
     }
     __syncthreads();
 
-    for (int g = 0;; ++g) {
+    for (int g = 0; g < a.iter_budget; ++g) {
         int any = 0;
         for (int p = threadIdx.x; p < a.P; p += THREADS) any |= (s_status[p] == kRunning);
         if (!__syncthreads_or(any)) break;
@@ -704,7 +721,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
                 st = CCS_STALLED;
             } else {
                 const long long r0 = __ldcg(&P.ctrl->r0);
-                const int it = g + 1;
+                const int it = s_base[p] + g + 1;
                 st = (r0 == 0) ? CCS_CONVERGED : (it >= a.max_iter ? CCS_MAX_ITER : kRunning);
                 if (blockIdx.x == 0) {
                     P.ctrl->iteration = it;
@@ -867,8 +884,15 @@ static int blocks_per_sm(int dev, engine_fn fn, int threads, size_t smem) {
 
 // Launch the engine on P problems whose arrays are already carved out in
 // `pds` (ctrl pointers into the header of `ws`).  Fills out[0..P).
-int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, char *ws,
-               cudaStream_t s, ccs_result *dev_out) {
+// Launch shape of one engine launch: kernel instance, threads, shared
+// memory plan, grid.  Marks each problem's kPdUseFp flag.
+struct LaunchPlan {
+    engine_fn fn;
+    int threads, stages, queue_cap, G;
+    size_t fp_cap, stage_bytes, smem;
+};
+
+static int plan_launch(ProblemDev *pds, int P, const ccs_params &prm, LaunchPlan &L) {
     int dmax = 1;
     bool aligned = true;
     for (int p = 0; p < P; ++p) {
@@ -893,7 +917,8 @@ int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, c
     }
     const size_t stage_bytes = align_up((size_t)(warps - 1) * tpw * kTile * dmax * 4, 128);
     const size_t entry = (size_t)(dmax + 1) * 4;  // one queued candidate
-    const size_t status_bytes = align_up((size_t)P, 16) + sizeof(long long) * (size_t)(P + 1);
+    const size_t status_bytes = align_up((size_t)P, 16) + sizeof(long long) * (size_t)(P + 1) +
+                                sizeof(int) * (size_t)P;
     if (P > kMaxProblems) {
         set_last_error("at most %d problems per launch (got %d)", kMaxProblems, P);
         return CCS_EINVAL;
@@ -909,8 +934,8 @@ int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, c
     for (int p = 0; p < P; ++p) {
         ProblemDev &pd = pds[p];
         const size_t need = align_up((size_t)pd.m, 16);
-        pd.pad = need <= fp_budget ? 1 : 0;
-        if (pd.pad) fp_cap = std::max(fp_cap, need);
+        pd.flags = (pd.flags & ~kPdUseFp) | (need <= fp_budget ? kPdUseFp : 0);
+        if (pd.flags & kPdUseFp) fp_cap = std::max(fp_cap, need);
     }
     fp_cap = align_up(fp_cap, 128);
     const int stages =
@@ -931,19 +956,40 @@ int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, c
         return CCS_ECUDA;
     }
     const int G = std::min(kMaxBlocks, di.sms);
+    L.fn = fn;
+    L.threads = threads;
+    L.stages = stages;
+    L.queue_cap = queue_cap;
+    L.G = G;
+    L.fp_cap = fp_cap;
+    L.stage_bytes = stage_bytes;
+    L.smem = smem;
+    return CCS_OK;
+}
 
-    EngineArgs a;
+static void fill_args(EngineArgs &a, const LaunchPlan &L, int P, const ccs_params &prm) {
     std::memset(&a, 0, sizeof(a));
     a.P = P;
     a.alpha = prm.alpha;
     a.mode = prm.score_mode;
     a.max_iter = prm.max_iter;
-    a.fp_cap = (int)fp_cap;
-    a.stages = stages;
-    a.stage_bytes = (int)stage_bytes;
-    a.queue_cap = queue_cap;
+    a.fp_cap = (int)L.fp_cap;
+    a.stages = L.stages;
+    a.stage_bytes = (int)L.stage_bytes;
+    a.queue_cap = L.queue_cap;
     a.watchdog_ns = (long long)(prm.watchdog_ms > 0 ? prm.watchdog_ms : 2000) * 1000000ll;
     a.debug_flags = prm.debug_flags;
+    a.iter_budget = 0x7fffffff;
+}
+
+
+int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, char *ws,
+               cudaStream_t s, ccs_result *dev_out) {
+    LaunchPlan L;
+    int rc = plan_launch(pds, P, prm, L);
+    if (rc) return rc;
+    EngineArgs a;
+    fill_args(a, L, P, prm);
     a.sync = reinterpret_cast<EngineSync *>(ws);
     char *e = ws + sync_bytes(P);
     unsigned long long *stamps = reinterpret_cast<unsigned long long *>(e);
@@ -968,7 +1014,8 @@ int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, c
 
     void *args[] = {&a};
     const int ev = prof_start(CCS_K_PERSISTENT, s);
-    CCS_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)fn, dim3(G), dim3(threads), args, smem, s));
+    CCS_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)L.fn, dim3(L.G), dim3(L.threads), args,
+                                             L.smem, s));
     prof_stop(ev, s);
     count_launches(1);
     if (dev_out) return CCS_OK;  // asynchronous: the kernel writes the results
@@ -1028,6 +1075,52 @@ int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, c
     if (herr) {
         set_last_error("a bounded device wait exceeded the watchdog (%d ms)",
                        prm.watchdog_ms > 0 ? prm.watchdog_ms : 2000);
+        return CCS_ETIMEOUT;
+    }
+    return CCS_OK;
+}
+
+// Resume-mode header: [EngineSync | P ccs_result] [stamps] [P descriptors].
+static size_t resume_results_bytes(int P) {
+    return align_up(sizeof(EngineSync) + sizeof(ccs_result) * (size_t)P, 256);
+}
+
+size_t engine_resume_header_bytes(int P) {
+    return resume_results_bytes(P) + stamps_bytes() + align_up(sizeof(ProblemDev) * (size_t)P, 256);
+}
+
+int engine_resume(ProblemDev *pds, int P, const ccs_params &prm, int iter_budget, ccs_result *out,
+                  char *hdr, cudaStream_t s) {
+    LaunchPlan L;
+    int rc = plan_launch(pds, P, prm, L);
+    if (rc) return rc;
+    EngineArgs a;
+    fill_args(a, L, P, prm);
+    a.resume = 1;
+    a.iter_budget = iter_budget > 0 ? iter_budget : 1;
+    a.sync = reinterpret_cast<EngineSync *>(hdr);
+    a.dev_out = reinterpret_cast<ccs_result *>(hdr + sizeof(EngineSync));
+    ProblemDev *d_probs =
+        reinterpret_cast<ProblemDev *>(hdr + resume_results_bytes(P) + stamps_bytes());
+    a.probs = d_probs;
+    CCS_CUDA_TRY(cudaMemsetAsync(hdr, 0, sizeof(EngineSync), s));
+    CCS_CUDA_TRY(cudaMemcpyAsync(d_probs, pds, sizeof(ProblemDev) * P, cudaMemcpyHostToDevice, s));
+    void *args[] = {&a};
+    const int ev = prof_start(CCS_K_PERSISTENT, s);
+    CCS_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)L.fn, dim3(L.G), dim3(L.threads), args,
+                                             L.smem, s));
+    prof_stop(ev, s);
+    count_launches(1);
+    const size_t bytes = sizeof(EngineSync) + sizeof(ccs_result) * (size_t)P;
+    std::vector<char> h(bytes);
+    CCS_CUDA_TRY(cudaMemcpyAsync(h.data(), hdr, bytes, cudaMemcpyDeviceToHost, s));
+    CCS_CUDA_TRY(cudaStreamSynchronize(s));
+    EngineSync hs;
+    std::memcpy(&hs, h.data(), sizeof(hs));
+    std::memcpy(out, h.data() + sizeof(EngineSync), sizeof(ccs_result) * (size_t)P);
+    if (hs.error) {
+        for (int p = 0; p < P; ++p) out[p].error = CCS_ETIMEOUT;
+        set_last_error("a bounded device wait exceeded the watchdog");
         return CCS_ETIMEOUT;
     }
     return CCS_OK;

@@ -16,6 +16,11 @@ constexpr int kSlotRec = 16;        // ints per row record: count, then kSlots c
 constexpr int kMaxSortRow = 32768;  // longest CSR row sorted on chip
 constexpr int kRunning = -1;        // DecodeCtrl::status while iterating
 
+enum ProblemFlags : int {
+    kPdUseFp = 1,
+    kPdFresh = 2,
+};
+
 enum ErrorBits : int {
     kErrWatchdog = 1,
 };
@@ -35,7 +40,9 @@ static_assert(sizeof(DecodeCtrl) == 64, "DecodeCtrl layout");
 
 // Device view of one problem plus its slice of the workspace.
 struct ProblemDev {
-    int n, m, d, pad;
+    int n, m, d;
+    int flags;            // kPdUseFp: fingerprints fit shared memory (engine);
+                          // kPdFresh: initialise before iterating (resume mode)
     const int32_t *csc_rows;
     const int64_t *csr_ptr;
     const int32_t *csr_cols;
@@ -141,6 +148,14 @@ size_t engine_header_bytes(int P);
 DecodeCtrl *header_ctrl(char *ws, int p);
 int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, char *ws,
                cudaStream_t s, ccs_result *dev_out = nullptr);
+// Resume mode (serving): the control blocks live with each problem
+// (pds[p].ctrl) and persist between launches; problems flagged kPdFresh are
+// initialised, the others continue from their saved state; at most
+// iter_budget iterations run; out[p].status is -1 for problems still
+// running.  `hdr` needs engine_resume_header_bytes(P) bytes.
+size_t engine_resume_header_bytes(int P);
+int engine_resume(ProblemDev *pds, int P, const ccs_params &prm, int iter_budget, ccs_result *out,
+                  char *hdr, cudaStream_t s);
 int check_params(const ccs_params *p, int d);
 
 }  // namespace ccs

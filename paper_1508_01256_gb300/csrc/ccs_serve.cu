@@ -1,0 +1,344 @@
+// ccs_serve.cu -- continuous-batching decode server.
+//
+// A worker thread owns one stream and runs engine rounds: each round is one
+// persistent launch over every admitted request, at most `iters_per_round`
+// Parallel-l0 iterations, with each request's state (x_hat, r, fingerprints,
+// slot records, control block) kept on the device between rounds.  After a
+// round, finished requests are retired (their state memory returns to the
+// pool) and pending requests are admitted as memory and batch slots allow,
+// so requests that arrive while others are on the GPU join the next round
+// and their work overlaps on the device.  Results are bit-identical to a
+// decode of the same request alone: every problem's iteration depends only
+// on its own data.
+//
+// Memory: the caller hands over one device pool; the server sub-allocates
+// each admitted request's state from it (first fit, 256-byte aligned) and the
+// launch header once.  A request whose state can never fit is refused at
+// submission (CCS_EBUDGET); one that does not fit now waits in the queue.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "ccs_internal.cuh"
+
+namespace ccs {
+
+namespace {
+
+double now_s() {
+    using clk = std::chrono::steady_clock;
+    static const clk::time_point t0 = clk::now();
+    return std::chrono::duration<double>(clk::now() - t0).count();
+}
+
+// First-fit allocator over [0, size) with coalescing free list.
+class PoolAllocator {
+  public:
+    explicit PoolAllocator(size_t size) : size_(size) { free_[0] = size; }
+    bool alloc(size_t bytes, size_t &off) {
+        bytes = align_up(bytes, 256);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                off = it->first;
+                const size_t rest = it->second - bytes;
+                free_.erase(it);
+                if (rest) free_[off + bytes] = rest;
+                used_ += bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = align_up(bytes, 256);
+        used_ -= bytes;
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && off + bytes == next->first) {
+            bytes += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                prev->second += bytes;
+                return;
+            }
+        }
+        free_[off] = bytes;
+    }
+    size_t used() const { return used_; }
+    size_t size() const { return size_; }
+
+  private:
+    size_t size_, used_ = 0;
+    std::map<size_t, size_t> free_;
+};
+
+struct Request {
+    int64_t ticket;
+    ccs_problem prob;
+    size_t state_bytes = 0, off = 0;
+    bool fresh = true;
+    int rounds = 0;
+    double submit_s = 0, admit_s = 0, done_s = 0;
+    ccs_result result{};
+};
+
+}  // namespace
+
+}  // namespace ccs
+
+struct ccs_server {
+    ccs_server_config cfg;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    char *pool = nullptr;
+    size_t header_off = 0;
+    ccs::PoolAllocator *alloc = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<ccs::Request> pending;
+    std::vector<ccs::Request> inflight;
+    std::unordered_map<int64_t, ccs::Request> finished;
+    int64_t next_ticket = 1;
+    bool stop = false;
+    int error = CCS_OK;
+    ccs_server_stats stats{};
+    std::thread worker;
+};
+
+namespace ccs {
+
+static size_t request_state_bytes(int32_t n, int32_t m) {
+    return align_up(sizeof(DecodeCtrl), 256) + decode_ws_layout(n, m, nullptr, nullptr);
+}
+
+static void worker_loop(ccs_server *S) {
+    cudaSetDevice(S->device);
+    const int maxb = S->cfg.max_batch;
+    std::vector<ProblemDev> pds;
+    std::vector<ccs_result> res(maxb);
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            // admit pending requests in arrival order while memory and slots allow
+            for (auto it = S->pending.begin();
+                 it != S->pending.end() && (int)S->inflight.size() < maxb;) {
+                size_t off;
+                if (S->alloc->alloc(it->state_bytes, off)) {
+                    it->off = off;
+                    it->admit_s = now_s();
+                    S->inflight.push_back(*it);
+                    it = S->pending.erase(it);
+                    S->stats.admitted += 1;
+                } else {
+                    break;  // first come, first served: no overtaking
+                }
+            }
+            if (S->inflight.empty()) {
+                if (S->stop) return;
+                S->cv_work.wait(lk, [&] { return S->stop || !S->pending.empty(); });
+                continue;
+            }
+            const int64_t bytes = (int64_t)S->alloc->used();
+            if (bytes > S->stats.peak_bytes) S->stats.peak_bytes = bytes;
+            if ((int64_t)S->inflight.size() > S->stats.peak_inflight)
+                S->stats.peak_inflight = (int64_t)S->inflight.size();
+        }
+        // build this round's problem list (the worker alone touches inflight
+        // entries' device state; submitters only append to `pending`)
+        const int P = (int)S->inflight.size();
+        pds.assign(P, ProblemDev{});
+        int rc = CCS_OK;
+        for (int p = 0; p < P && rc == CCS_OK; ++p) {
+            Request &R = S->inflight[p];
+            ProblemDev &D = pds[p];
+            D.n = R.prob.n;
+            D.m = R.prob.m;
+            D.d = R.prob.d;
+            D.csc_rows = R.prob.csc_rows;
+            D.csr_ptr = R.prob.csr_ptr;
+            D.csr_cols = R.prob.csr_cols;
+            D.y = R.prob.y;
+            D.x_hat = R.prob.x_hat;
+            D.r = R.prob.r;
+            D.r0_hist = R.prob.r0_hist;
+            char *base = S->pool + R.off;
+            D.ctrl = reinterpret_cast<DecodeCtrl *>(base);
+            decode_ws_layout(D.n, D.m, &D, base + align_up(sizeof(DecodeCtrl), 256));
+            D.flags = R.fresh ? kPdFresh : 0;
+            if (R.fresh && cudaMemsetAsync(D.ctrl, 0, sizeof(DecodeCtrl), S->stream) != cudaSuccess)
+                rc = CCS_ECUDA;
+        }
+        if (rc == CCS_OK)
+            rc = engine_resume(pds.data(), P, S->cfg.params, S->cfg.iters_per_round, res.data(),
+                               S->pool + S->header_off, S->stream);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->stats.rounds += 1;
+            std::vector<Request> keep;
+            keep.reserve(P);
+            const double t = now_s();
+            for (int p = 0; p < P; ++p) {
+                Request &R = S->inflight[p];
+                R.rounds += 1;
+                R.fresh = false;
+                const bool done = rc != CCS_OK || res[p].status != kRunning || res[p].error;
+                if (done) {
+                    R.result = res[p];
+                    if (rc != CCS_OK) R.result.error = rc;
+                    R.done_s = t;
+                    S->alloc->release(R.off, R.state_bytes);
+                    S->finished[R.ticket] = R;
+                    S->stats.completed += 1;
+                } else {
+                    keep.push_back(R);
+                }
+            }
+            S->inflight.swap(keep);
+            if (rc != CCS_OK) S->error = rc;
+        }
+        S->cv_done.notify_all();
+    }
+}
+
+}  // namespace ccs
+
+using namespace ccs;
+
+extern "C" int ccs_server_create(const ccs_server_config *cfg, ccs_stream_t stream,
+                                 ccs_server **out) {
+    if (!cfg || !out || !cfg->pool || cfg->max_batch < 1 || cfg->max_batch > 4096 ||
+        cfg->iters_per_round < 1) {
+        set_last_error("ccs_server_create: bad configuration");
+        return CCS_EINVAL;
+    }
+    const size_t hdr = align_up(engine_resume_header_bytes(cfg->max_batch), 256);
+    if (cfg->pool_bytes <= hdr) {
+        set_last_error("ccs_server_create: pool of %zu bytes cannot hold the %zu-byte launch header",
+                       cfg->pool_bytes, hdr);
+        return CCS_EBUDGET;
+    }
+    ccs_server *S = new ccs_server();
+    S->cfg = *cfg;
+    if (cudaGetDevice(&S->device) != cudaSuccess) {
+        delete S;
+        return cuda_fail(cudaGetLastError(), "cudaGetDevice");
+    }
+    S->stream = reinterpret_cast<cudaStream_t>(stream);
+    S->pool = static_cast<char *>(cfg->pool);
+    S->header_off = cfg->pool_bytes - hdr;  // launch header at the top of the pool
+    S->alloc = new PoolAllocator(S->header_off);
+    S->worker = std::thread(worker_loop, S);
+    *out = S;
+    return CCS_OK;
+}
+
+extern "C" int ccs_server_submit(ccs_server *S, const ccs_problem *req, int64_t *ticket) {
+    if (!S || !req || !ticket) {
+        set_last_error("ccs_server_submit: null argument");
+        return CCS_EINVAL;
+    }
+    int rc = check_sizes(req->n, req->m, req->d);
+    if (rc) return rc;
+    if ((rc = check_params(&S->cfg.params, req->d))) return rc;
+    if (!req->csc_rows || !req->csr_ptr || !req->csr_cols || !req->y || !req->x_hat || !req->r ||
+        (reinterpret_cast<uintptr_t>(req->csc_rows) & 15u)) {
+        set_last_error("ccs_server_submit: null or misaligned array");
+        return CCS_EINVAL;
+    }
+    Request R;
+    R.prob = *req;
+    R.state_bytes = request_state_bytes(req->n, req->m);
+    if (align_up(R.state_bytes, 256) > S->alloc->size()) {
+        set_last_error("ccs_server_submit: request needs %zu bytes of state, pool holds %zu",
+                       R.state_bytes, S->alloc->size());
+        return CCS_EBUDGET;
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop) {
+            set_last_error("ccs_server_submit: server is shutting down");
+            return CCS_EBUSY;
+        }
+        R.ticket = S->next_ticket++;
+        R.submit_s = now_s();
+        S->pending.push_back(R);
+        S->stats.submitted += 1;
+        *ticket = R.ticket;
+    }
+    S->cv_work.notify_one();
+    return CCS_OK;
+}
+
+static void fill_info(const Request &R, ccs_ticket_info *info) {
+    info->result = R.result;
+    info->submit_s = R.submit_s;
+    info->admit_s = R.admit_s;
+    info->done_s = R.done_s;
+    info->rounds = R.rounds;
+    info->reserved = 0;
+}
+
+extern "C" int ccs_server_poll(ccs_server *S, int64_t ticket, ccs_ticket_info *info) {
+    if (!S || !info) return CCS_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->finished.find(ticket);
+    if (it == S->finished.end()) {
+        if (ticket <= 0 || ticket >= S->next_ticket) {
+            set_last_error("ccs_server_poll: unknown ticket %lld", (long long)ticket);
+            return CCS_EINVAL;
+        }
+        return CCS_EBUSY;
+    }
+    fill_info(it->second, info);
+    S->finished.erase(it);
+    return CCS_OK;
+}
+
+extern "C" int ccs_server_wait(ccs_server *S, int64_t ticket, ccs_ticket_info *info,
+                               int32_t timeout_ms) {
+    if (!S || !info) return CCS_EINVAL;
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (ticket <= 0 || ticket >= S->next_ticket) {
+        set_last_error("ccs_server_wait: unknown ticket %lld", (long long)ticket);
+        return CCS_EINVAL;
+    }
+    const auto ready = [&] { return S->finished.count(ticket) != 0; };
+    if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms), ready))
+        return CCS_EBUSY;
+    auto it = S->finished.find(ticket);
+    fill_info(it->second, info);
+    S->finished.erase(it);
+    return CCS_OK;
+}
+
+extern "C" int ccs_server_stats_get(ccs_server *S, ccs_server_stats *out) {
+    if (!S || !out) return CCS_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    *out = S->stats;
+    out->bytes_in_use = (int64_t)S->alloc->used();
+    out->pending = (int64_t)S->pending.size();
+    out->inflight = (int64_t)S->inflight.size();
+    out->error = S->error;
+    return CCS_OK;
+}
+
+extern "C" int ccs_server_destroy(ccs_server *S) {
+    if (!S) return CCS_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    const int err = S->error;
+    delete S->alloc;
+    delete S;
+    return err;
+}

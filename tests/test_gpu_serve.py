@@ -1,0 +1,119 @@
+"""Serving: continuous batching of decode requests (ccs_server_*).
+
+Each served result must be bit-identical to the same request decoded alone,
+whatever else shares its rounds; admission must respect the memory pool; a
+request that can never fit is refused."""
+import random
+import time
+
+import numpy as np
+import pytest
+
+from paper_1508_01256_gb300 import inputs
+from gpu_util import device_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ccs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1508_01256_gb300 import build, ccs
+    build.build()
+    return ccs
+
+
+def _requests(ccs, probs):
+    import torch
+    reqs = []
+    for p in probs:
+        csc, ptr, cols, y = device_problem(ccs, p)
+        x_hat = torch.full((p.n,), float("nan"), dtype=torch.float64, device="cuda")
+        r = torch.full((p.m,), float("nan"), dtype=torch.float64, device="cuda")
+        hist = torch.full((101,), -1, dtype=torch.int64, device="cuda")
+        reqs.append((csc, ptr, cols, y, x_hat, r, hist))
+    return reqs
+
+
+def _check_same_as_alone(ccs, reqs, infos):
+    for (csc, ptr, cols, y, x_hat, r, hist), info in zip(reqs, infos):
+        alone = ccs.decode_parallel_l0(csc, ptr, cols, y)
+        res = info.result
+        assert res.error == 0
+        assert (res.status, res.iterations, res.r0_final) == \
+            (alone.status, alone.iterations, alone.r0_final)
+        assert np.array_equal(x_hat.cpu().numpy(), alone.x_hat.cpu().numpy())
+        assert np.array_equal(r.cpu().numpy(), alone.r.cpu().numpy())
+        assert hist[:res.iterations + 1].cpu().tolist() == alone.r0_hist
+
+
+@pytest.mark.parametrize("iters_per_round", [1, 3])
+def test_served_results_equal_alone(ccs, iters_per_round):
+    """Mixed sizes arriving at random times join running rounds; every result
+    equals the request decoded alone."""
+    probs = inputs.batch_problems(24, seed=17 + iters_per_round, log2n_hi=17.0, ds=(7, 9))
+    reqs = _requests(ccs, probs)
+    rng = random.Random(5)
+    arrivals = np.cumsum([rng.uniform(0, 0.002) for _ in reqs])
+    with ccs.Server(512 << 20, max_batch=8, iters_per_round=iters_per_round) as srv:
+        infos = ccs.serve_poisson(srv, reqs, arrivals)
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["error"] == 0
+    assert st["peak_inflight"] <= 8
+    assert all(i.done_s >= i.admit_s >= i.submit_s for i in infos)
+    _check_same_as_alone(ccs, reqs, infos)
+
+
+def test_admission_by_memory_budget(ccs):
+    """A pool that holds about two requests' state at a time: the rest wait,
+    every request still completes with the alone result, and the state in use
+    never exceeds the pool."""
+    probs = [inputs.make_problem(200000, 20000, 7, 2000, 300 + i) for i in range(6)]
+    reqs = _requests(ccs, probs)
+    one = ccs.ccs_workspace_size(ccs.OP_DECODE, 200000, 20000, 7)
+    pool = int(2.5 * one) + (64 << 10)  # room for two states and the launch header
+    with ccs.Server(pool, max_batch=16, iters_per_round=2) as srv:
+        infos = ccs.serve_poisson(srv, reqs, [0.0] * len(reqs))
+        st = srv.stats()
+    assert st["completed"] == 6 and st["peak_inflight"] <= 2
+    assert st["peak_bytes"] <= pool
+    assert max(i.admit_s for i in infos) > min(i.done_s for i in infos)  # someone waited
+    _check_same_as_alone(ccs, reqs, infos)
+
+
+def test_refuses_request_that_cannot_fit(ccs):
+    import torch
+    p = inputs.make_problem(300000, 50000, 7, 100, 9)
+    csc, ptr, cols, y = device_problem(ccs, p)
+    x_hat = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    r = torch.empty(p.m, dtype=torch.float64, device="cuda")
+    with ccs.Server(2 << 20, max_batch=4) as srv:  # the request needs ~3.7 MB of state
+        with pytest.raises(ccs.CcsError) as ei:
+            srv.submit(csc, ptr, cols, y, x_hat, r)
+        assert ei.value.code == ccs.CCS_EBUDGET
+        # a bad request is refused without disturbing the server
+        with pytest.raises(ccs.CcsError) as ei:
+            srv.submit(csc, ptr, cols, y, x_hat, None)
+        assert ei.value.code == ccs.CCS_EINVAL
+
+
+def test_poll_reports_busy_then_done(ccs):
+    probs = [inputs.plain_small(seed=s) for s in range(3)]
+    reqs = _requests(ccs, probs)
+    with ccs.Server(256 << 20, max_batch=4, iters_per_round=1) as srv:
+        tickets = [srv.submit(*q) for q in reqs]
+        infos = []
+        deadline = time.time() + 30
+        for t in tickets:
+            while True:
+                info = srv.poll(t)
+                if info is not None:
+                    infos.append(info)
+                    break
+                assert time.time() < deadline
+                time.sleep(0.001)
+        with pytest.raises(ccs.CcsError):
+            srv.poll(999999)
+    _check_same_as_alone(ccs, reqs, infos)
