@@ -279,6 +279,62 @@ def batched_vs_plain(ccs, dev, count: int, seed: int, reps: int = 3):
                         "k/m in {0.05,0.1,0.2}, d in {5,7,9,11}, gauss-grid"}
 
 
+def serving_run(ccs, dev, count: int, seed: int, load: float = 0.7,
+                pool_bytes: int = 8 << 30, max_batch: int = 512, iters_per_round: int = 2):
+    """Serving workload: `count` requests, n log-uniform 2^12..2^22, delta,
+    rho as in the batched workload, d in {7, 9}.  First all of them at once
+    (the server's peak decodes/s), then Poisson arrivals at `load` x that
+    rate; latency = result ready - submission, from the library's clock."""
+    import random
+
+    import numpy as np
+    import torch
+
+    from paper_1508_01256_gb300 import inputs
+    shapes = inputs.batch_shapes(count, seed=seed, log2n_hi=22.0, ds=(7, 9))
+    reqs, probs = [], []
+    for q, (n, m, d, k) in enumerate(shapes):
+        p = inputs.make_problem(n, m, d, k, seed * 7919 + q)
+        csc, ptr, cols = ccs.make_expander(p.n, p.m, p.d, p.a_seed, device=dev)
+        y = ccs.measure(ptr, cols, torch.from_numpy(p.x).to(dev), p.m, p.d)
+        reqs.append((csc, ptr, cols, y, torch.empty(p.n, dtype=torch.float64, device=dev),
+                     torch.empty(p.m, dtype=torch.float64, device=dev)))
+        probs.append(p)
+    torch.cuda.synchronize()
+    with ccs.Server(pool_bytes, max_batch=max_batch, iters_per_round=iters_per_round) as srv:
+        infos = ccs.serve_poisson(srv, reqs, [0.0] * count)
+        closed = count / (max(i.done_s for i in infos) - min(i.submit_s for i in infos))
+        rate = load * closed
+        rng = np.random.default_rng(seed)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
+        infos = ccs.serve_poisson(srv, reqs, arrivals)
+        st = srv.stats()
+    lat_ms = sorted(1000.0 * (i.done_s - i.submit_s) for i in infos)
+    span = max(i.done_s for i in infos) - min(i.submit_s for i in infos)
+    # each served result equals the request decoded alone (a sample)
+    same = True
+    for q in random.Random(seed).sample(range(count), min(12, count)):
+        csc, ptr, cols, y, x_hat, r = reqs[q]
+        alone = ccs.decode_parallel_l0(csc, ptr, cols, y, history=False)
+        res = infos[q].result
+        same &= (res.status, res.iterations, res.r0_final) == \
+            (alone.status, alone.iterations, alone.r0_final)
+        same &= bool(torch.equal(x_hat, alone.x_hat)) and bool(torch.equal(r, alone.r))
+    exact = sum(int(i.result.status == ccs.CONVERGED and
+                    bool((reqs[q][4].cpu().numpy() == probs[q].x).all()))
+                for q, i in enumerate(infos))
+    return {"requests": count, "offered_rate_per_s": rate, "load": load,
+            "peak_decodes_per_s": closed, "decodes_per_s": count / span,
+            "p50_ms": lat_ms[len(lat_ms) // 2], "p99_ms": lat_ms[min(len(lat_ms) - 1,
+                                                                  int(0.99 * len(lat_ms)))],
+            "max_ms": lat_ms[-1], "rounds": st["rounds"], "peak_inflight": st["peak_inflight"],
+            "peak_state_bytes": st["peak_bytes"], "pool_bytes": pool_bytes,
+            "iters_per_round": iters_per_round, "same_results_sample": same,
+            "exact_recovery": exact,
+            "workload": "n log-uniform 2^12..2^22, m/n in {0.01,0.05,0.1,0.3}, "
+                        "k/m in {0.05,0.1,0.2}, d in {7,9}, Poisson arrivals"}
+
+
 def run_reference(args):
     from paper_1508_01256_gb300 import inputs  # noqa: F401  (inputs only)
     rank = int(os.environ.get("RANK", "0"))
@@ -474,6 +530,9 @@ def run_ccs(args):
     batched = None
     if args.batch > 0:
         batched = batched_vs_plain(ccs, dev, args.batch, seed=1000 * rank + 4242)
+    serving = None
+    if args.serve > 0:
+        serving = serving_run(ccs, dev, args.serve, seed=1000 * rank + 777)
 
     if rank == 0:
         cb = None
@@ -499,6 +558,7 @@ def run_ccs(args):
                 "exact_recovery": exact,
                 "kernel_times": kernel_share,
                 "batched": batched,
+                "serving": serving,
                 "wall_s_timed_region": wall}
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -520,6 +580,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=512,
                     help="problems in the batched-vs-plain comparison (0: skip)")
+    ap.add_argument("--serve", type=int, default=256,
+                    help="requests in the serving run (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
