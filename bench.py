@@ -97,6 +97,23 @@ def traffic_record(kernel: str, workload_name: str):
     return entry["bytes_per_launch"] if sha == entry.get("source_sha") else None
 
 
+def slowest_over_ranks(times, dist=None, device=None):
+    """Each timing's maximum over the ranks of the job (the slowest rank
+    defines the job's time); the local values when there is no process group."""
+    if dist is None:
+        return [float(t) for t in times]
+    import torch
+    t = torch.tensor([float(x) for x in times], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu().tolist()]
+
+
+def job_rate(units_per_rank: float, world: int, slowest_s: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (every rank does the same amount of work)."""
+    return world * units_per_rank / slowest_s
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason samples (every 200 ms) from before
     the warm-up to the end of the end-to-end loop, which brackets the timed
@@ -491,12 +508,9 @@ def run_ccs(args):
 
     # max over ranks
     decodes = args.steps
-    if dist is not None:
-        tt = torch.tensor([total_s, e2e_t], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_s, e2e_t = float(tt[0]), float(tt[1])
-    value = world * decodes / total_s
-    e2e_value = world * e2e_steps / e2e_t
+    total_s, e2e_t = slowest_over_ranks([total_s, e2e_t], dist, dev)
+    value = job_rate(decodes, world, total_s)
+    e2e_value = job_rate(e2e_steps, world, e2e_t)
 
     # roofline of the dominant kernel.  Algorithmic bytes of one iteration:
     # 4 d n (every column's d row indices) + 8 m (one read of r); a decode
