@@ -278,17 +278,31 @@ def batched_vs_plain(ccs, dev, count: int, seed: int, reps: int = 3):
         torch.cuda.synchronize()
         if rep:
             tp.append(ev[0].elapsed_time(ev[1]))
+    # the same batch captured once in a CUDA graph and replayed
+    graph = ccs.BatchGraph(pbs, prm, dev)
+    tg = []
+    for rep in range(reps + 1):
+        flush.zero_()
+        ev[0].record(stream)
+        graph.launch(stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        if rep:
+            tg.append(ev[0].elapsed_time(ev[1]))
+    rg = graph.read_results()
+    graph.close()
     rb = ccs.results_from_device(res_b, count)
     rp = ccs.results_from_device(res_p, count)
-    same = all(a.status == b.status and a.iterations == b.iterations and a.r0_final == b.r0_final
-               for a, b in zip(rb, rp))
+    same = all(a.status == b.status == c.status and a.iterations == b.iterations == c.iterations
+               and a.r0_final == b.r0_final == c.r0_final for a, b, c in zip(rb, rp, rg))
     conv = sum(a.status == ccs.CONVERGED for a in rb)
     exact = sum(a.status == ccs.CONVERGED and bool((outs[i][0].cpu().numpy() == items[i][0].x).all())
                 for i, a in enumerate(rb))
-    mb, mp = statistics.median(tb), statistics.median(tp)
+    mb, mp, mg = statistics.median(tb), statistics.median(tp), statistics.median(tg)
     cols_total = sum(p.n * a.iterations for p, a in zip(probs, rb))
     return {"problems": count, "batched_decodes_per_s": count / (mb / 1000.0),
             "plain_decodes_per_s": count / (mp / 1000.0), "batched_ms": mb, "plain_ms": mp,
+            "graph_batched_decodes_per_s": count / (mg / 1000.0), "graph_ms": mg,
             "speedup": mp / mb, "batched_column_updates_per_s": cols_total / (mb / 1000.0),
             "same_results": same, "converged": conv, "exact_recovery": exact,
             "max_iterations": max(a.iterations for a in rb),

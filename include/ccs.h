@@ -247,6 +247,24 @@ CCS_API int ccs_decode_batch_async(const ccs_problem *probs, int32_t count,
                                    const ccs_params *p, ccs_result *out_dev,
                                    void *ws, size_t ws_bytes, ccs_stream_t stream);
 
+/* ---- CUDA graph of a batched decode -----------------------------------------
+ *
+ * ccs_batch_graph_create captures one ccs_decode_batch_async launch of these
+ * problems (the launch header reset and the persistent kernel) into a CUDA
+ * graph; the problem descriptors are uploaded to the workspace once, now.
+ * Each ccs_graph_launch replays the whole decode of every problem on the
+ * same device arrays and workspace (write new y values in place between
+ * replays to decode new measurements), results to DEVICE memory out_dev as
+ * for ccs_decode_batch_async.  Replays on one graph must not overlap.  The
+ * workspace, arrays and out_dev must outlive the graph.  Synchronous during
+ * creation (it uploads and instantiates). */
+typedef struct ccs_graph ccs_graph;
+CCS_API int ccs_batch_graph_create(const ccs_problem *probs, int32_t count,
+                                   const ccs_params *p, ccs_result *out_dev,
+                                   void *ws, size_t ws_bytes, ccs_graph **out);
+CCS_API int ccs_graph_launch(ccs_graph *g, ccs_stream_t stream);
+CCS_API int ccs_graph_destroy(ccs_graph *g);
+
 /* ---- serving: continuous batching -----------------------------------------
  *
  * A decode server with one worker thread.  Requests (ccs_problem: device

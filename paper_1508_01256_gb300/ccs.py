@@ -140,6 +140,12 @@ def lib() -> ctypes.CDLL:
         for name in ("ccs_server_create", "ccs_server_submit", "ccs_server_poll",
                      "ccs_server_wait", "ccs_server_stats_get", "ccs_server_destroy"):
             getattr(l, name).restype = ctypes.c_int
+        l.ccs_batch_graph_create.argtypes = [ctypes.POINTER(Problem), i32, ctypes.POINTER(Params),
+                                             P, P, sz, ctypes.POINTER(P)]
+        l.ccs_graph_launch.argtypes = [P, P]
+        l.ccs_graph_destroy.argtypes = [P]
+        for name in ("ccs_batch_graph_create", "ccs_graph_launch", "ccs_graph_destroy"):
+            getattr(l, name).restype = ctypes.c_int
         l.ccs_profile_begin.argtypes = []
         l.ccs_profile_end.argtypes = [ctypes.POINTER(KernelTime)]
         l.ccs_profile_phases.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
@@ -409,6 +415,42 @@ def decode_batch(items, alpha=2, max_iter=100, score_mode=SCORE_L0_DECREASE,
                                    iterations=rr.iterations, r0_final=rr.r0_final,
                                    error=rr.error))
     return result
+
+
+# ---- CUDA graph of a batched decode ----------------------------------------------
+
+class BatchGraph:
+    """A batched decode captured once (ccs_batch_graph_create), replayed by
+    launch().  Keeps the problems' tensors, workspace and result buffer."""
+
+    def __init__(self, probs, p: Params | None = None, device="cuda"):
+        self.probs = list(probs)
+        arr = (Problem * len(self.probs))(*self.probs)
+        self.ws = workspace(ccs_batch_workspace_size(self.probs), device)
+        self.results = result_buffer(len(self.probs), device)
+        self._h = ctypes.c_void_p()
+        _check(lib().ccs_batch_graph_create(arr, len(self.probs),
+                                            ctypes.byref(p) if p is not None else None,
+                                            _ptr(self.results), _ptr(self.ws),
+                                            self.ws.numel(), ctypes.byref(self._h)),
+               "ccs_batch_graph_create")
+
+    def launch(self, stream=None):
+        _check(lib().ccs_graph_launch(self._h, _stream(stream)), "ccs_graph_launch")
+
+    def read_results(self):
+        return results_from_device(self.results, len(self.probs))
+
+    def close(self):
+        if self._h:
+            lib().ccs_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- serving -------------------------------------------------------------------

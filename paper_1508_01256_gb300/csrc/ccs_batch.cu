@@ -25,7 +25,7 @@ extern "C" size_t ccs_batch_workspace_size(const ccs_problem *probs, int32_t cou
 
 static int decode_batch_impl(const ccs_problem *probs, int32_t count, const ccs_params *params,
                              ccs_result *out, void *ws, size_t ws_bytes, ccs_stream_t stream,
-                             ccs_result *dev_out) {
+                             ccs_result *dev_out, cudaGraphExec_t *capture = nullptr) {
     if (!probs || count < 1 || !out || !ws) {
         set_last_error("ccs_decode_batch: bad arguments");
         return CCS_EINVAL;
@@ -71,6 +71,13 @@ static int decode_batch_impl(const ccs_problem *probs, int32_t count, const ccs_
         P.ctrl = header_ctrl(hdr, q);
         base += decode_ws_layout(pr.n, pr.m, &P, base);
     }
+    if (capture) {
+        if (p.engine == CCS_ENGINE_HOST_LOOP) {
+            set_last_error("ccs_batch_graph_create: the host-driven engine cannot be captured");
+            return CCS_EINVAL;
+        }
+        return engine_capture(pds.data(), count, p, hdr, dev_out, capture);
+    }
     if (p.engine == CCS_ENGINE_HOST_LOOP) {
         if (dev_out) {
             set_last_error("ccs_decode_batch_async: the host-driven engine cannot run asynchronously");
@@ -101,4 +108,41 @@ extern "C" int ccs_decode_batch_async(const ccs_problem *probs, int32_t count,
     }
     std::vector<ccs_result> unused(count > 0 ? count : 1);
     return decode_batch_impl(probs, count, params, unused.data(), ws, ws_bytes, stream, out_dev);
+}
+
+struct ccs_graph {
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" int ccs_batch_graph_create(const ccs_problem *probs, int32_t count,
+                                      const ccs_params *params, ccs_result *out_dev, void *ws,
+                                      size_t ws_bytes, ccs_graph **out) {
+    if (!out || !out_dev) {
+        set_last_error("ccs_batch_graph_create: null argument");
+        return CCS_EINVAL;
+    }
+    ccs_graph *g = new ccs_graph();
+    std::vector<ccs_result> unused(count > 0 ? count : 1);
+    const int rc = decode_batch_impl(probs, count, params, unused.data(), ws, ws_bytes, nullptr,
+                                     out_dev, &g->exec);
+    if (rc != CCS_OK) {
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return CCS_OK;
+}
+
+extern "C" int ccs_graph_launch(ccs_graph *g, ccs_stream_t stream) {
+    if (!g || !g->exec) return CCS_EINVAL;
+    count_launches(1);
+    CCS_CUDA_TRY(cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)));
+    return CCS_OK;
+}
+
+extern "C" int ccs_graph_destroy(ccs_graph *g) {
+    if (!g) return CCS_EINVAL;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    delete g;
+    return CCS_OK;
 }

@@ -1080,6 +1080,46 @@ int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, c
     return CCS_OK;
 }
 
+// Capture one decode launch (header memset + cooperative kernel) into a CUDA
+// graph.  The descriptors are uploaded now, outside the capture; the graph
+// bakes the workspace and array pointers.  Results go to dev_out.
+int engine_capture(ProblemDev *pds, int P, const ccs_params &prm, char *ws, ccs_result *dev_out,
+                   cudaGraphExec_t *exec) {
+    LaunchPlan L;
+    int rc = plan_launch(pds, P, prm, L);
+    if (rc) return rc;
+    EngineArgs a;
+    fill_args(a, L, P, prm);
+    a.sync = reinterpret_cast<EngineSync *>(ws);
+    a.dev_out = dev_out;
+    a.stamps = nullptr;
+    if (P == 1) {
+        a.single = pds[0];
+        a.probs = nullptr;
+    } else {
+        ProblemDev *d_probs = reinterpret_cast<ProblemDev *>(ws + sync_bytes(P) + stamps_bytes());
+        CCS_CUDA_TRY(cudaMemcpy(d_probs, pds, sizeof(ProblemDev) * P, cudaMemcpyHostToDevice));
+        a.probs = d_probs;
+    }
+    cudaStream_t cs;
+    CCS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        void *args[] = {&a};
+        cudaError_t e1 = cudaMemsetAsync(ws, 0, sync_bytes(P), cs);
+        cudaError_t e2 = cudaLaunchCooperativeKernel((const void *)L.fn, dim3(L.G), dim3(L.threads),
+                                                     args, L.smem, cs);
+        e = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = (e1 != cudaSuccess) ? e1 : e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "capturing the engine launch");
+    return CCS_OK;
+}
+
 // Resume-mode header: [EngineSync | P ccs_result] [stamps] [P descriptors].
 static size_t resume_results_bytes(int P) {
     return align_up(sizeof(EngineSync) + sizeof(ccs_result) * (size_t)P, 256);

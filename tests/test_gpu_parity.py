@@ -381,3 +381,39 @@ def test_async_watchdog_reports_on_device(ccs):
                                      ccs.params(watchdog_ms=100, debug_flags=1), res_dev, ws)
     torch.cuda.synchronize()
     assert ccs.results_from_device(res_dev, 1)[0].error == ccs.CCS_ETIMEOUT
+
+
+def test_batch_graph_replays(ccs, orc):
+    """A batched decode captured in a CUDA graph: replays equal
+    ccs_decode_batch, and writing new measurements y in place then replaying
+    decodes the new signals (each against the oracle)."""
+    import torch
+    probs = inputs.batch_problems(10, seed=123, log2n_hi=15.0)
+    items = [device_problem(ccs, p) for p in probs]
+    outs, pbs = [], []
+    for (csc, ptr, cols, y), p in zip(items, probs):
+        x_hat = torch.empty(p.n, dtype=torch.float64, device="cuda")
+        r = torch.empty(p.m, dtype=torch.float64, device="cuda")
+        outs.append((x_hat, r))
+        pbs.append(ccs.problem(csc, ptr, cols, y, x_hat, r))
+    g = ccs.BatchGraph(pbs, ccs.params())
+    ref = ccs.decode_batch(items)
+    for _ in range(2):
+        g.launch()
+        torch.cuda.synchronize()
+        for (x_hat, r), rr, res in zip(outs, ref, g.read_results()):
+            assert res.status == rr.status and res.iterations == rr.iterations
+            assert torch.equal(x_hat, rr.x_hat) and torch.equal(r, rr.r)
+    # new signals on the same matrices, measured into the same y buffers
+    new = [inputs.make_problem(p.n, p.m, p.d, p.k, p.seed + 999) for p in probs]
+    for (csc, ptr, cols, y), p, q in zip(items, probs, new):
+        y.copy_(ccs.measure(ptr, cols, torch.from_numpy(q.x).cuda(), p.m, p.d))
+    g.launch()
+    torch.cuda.synchronize()
+    for (csc, ptr, cols, y), p, q, (x_hat, r), res in zip(items, probs, new, outs,
+                                                          g.read_results()):
+        A = orc.make_expander(p.n, p.m, p.d, p.a_seed)
+        oref = orc.parallel_l0(A, p.m, orc.measure(A, p.m, q.x))
+        assert res.status == oref["status"] and res.iterations == oref["iterations"]
+        assert np.array_equal(x_hat.cpu().numpy(), oref["x_hat"])
+    g.close()
