@@ -82,10 +82,22 @@ __global__ void __launch_bounds__(256) k_score(ProblemDev P, int alpha, int mode
 __global__ void __launch_bounds__(256) k_residual(ProblemDev P) {
     if (ld_volatile(&P.ctrl->status) != kRunning) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
     long long delta = 0;
+    bool touched = false, over = false;
+    int js[kSlotRec];
+    double s = 0.0;
     if (i < P.m && P.touched[i]) {
+        touched = true;
+        load_record(P, i, js);
+        over = js[0] > kSlots;
+        if (!over) s = row_sum_from_record(P, i, js);
+    }
+    const double so = overflow_row_sums(P, over, i, lane);  // whole warp
+    if (touched) {
+        if (over) s = so;
         P.touched[i] = 0;
-        const double rn = row_residual(P, i);
+        const double rn = __dsub_rn(P.y[i], s);
         const double ro = P.r[i];
         delta = (long long)(rn != 0.0) - (long long)(ro != 0.0);
         P.r[i] = rn;

@@ -15,13 +15,14 @@ namespace ccs {
 // 8-bit fingerprint of a residual entry: 0 exactly when the value is zero
 // (+0.0 or -0.0), otherwise a hash of its bits in 1..255.  Equal values have
 // equal fingerprints, so a fingerprint count bounds the count of any value.
-__device__ __forceinline__ uint8_t fingerprint(double v) {
-    const unsigned long long b = value_bits(v);
+__device__ __forceinline__ uint8_t fingerprint_of_bits(unsigned long long b) {
     if (b == 0ull) return 0;
     unsigned long long h = (b ^ (b >> 31)) * 0x9e3779b97f4a7c15ull;
     const unsigned f = (unsigned)(h >> 56);
     return (uint8_t)(f == 0u ? 1u : f);
 }
+
+__device__ __forceinline__ uint8_t fingerprint(double v) { return fingerprint_of_bits(value_bits(v)); }
 
 // Largest multiplicity of a nonzero byte among the first d bytes of the
 // packed words w0..w3 (4 bytes each, position t in byte t%4 of word t/4),
@@ -85,33 +86,31 @@ __device__ __forceinline__ bool exact_score_values(const unsigned long long (&v)
 // Equality is equality of binary64 values (bit patterns with -0.0 folded);
 // the mode is the most frequent nonzero value, ties to the numerically
 // smallest (order_key).  Score: Eq. (15) c_omega - c_0, or Alg. 8 c_omega.
-template <int DMAX>
+// With kPrefilter, before the O(d^2) comparison of 64-bit values the column
+// is tested against the fingerprint bound computed from the gathered values
+// (equal values have equal fingerprints), which rejects most columns exactly;
+// callers whose columns already passed a fingerprint test skip it.
+template <int DMAX, bool kPrefilter = true>
 __device__ __forceinline__ bool exact_score(const int32_t *rows, int d, const double *r,
                                             int alpha, int mode,
                                             unsigned long long *omega) {
     unsigned long long v[DMAX];
 #pragma unroll
     for (int t = 0; t < DMAX; ++t) v[t] = (t < d) ? value_bits(__ldcg(r + rows[t])) : 0ull;
+    if (!kPrefilter) return exact_score_values<DMAX>(v, d, alpha, mode, omega);
+    unsigned w[4] = {0u, 0u, 0u, 0u};
     int c0 = 0;
 #pragma unroll
-    for (int t = 0; t < DMAX; ++t) c0 += (t < d) & (v[t] == 0ull);
-    int best_cnt = 0;
-    unsigned long long best_bits = 0ull, best_key = ~0ull;
-#pragma unroll
-    for (int a = 0; a < DMAX; ++a) {
-        int c = 0;
-#pragma unroll
-        for (int b = 0; b < DMAX; ++b) c += (b < d) & (v[b] == v[a]);
-        const unsigned long long key = order_key(v[a]);
-        const bool better = (a < d) && (v[a] != 0ull) &&
-                            (c > best_cnt || (c == best_cnt && key < best_key));
-        best_cnt = better ? c : best_cnt;
-        best_key = better ? key : best_key;
-        best_bits = better ? v[a] : best_bits;
+    for (int t = 0; t < DMAX; ++t) {
+        const unsigned f = (t < d) ? (unsigned)fingerprint_of_bits(v[t]) : 0u;
+        c0 += (t < d) & (v[t] == 0ull);
+        w[t >> 2] |= f << (8 * (t & 3));
     }
-    const int score = (mode == CCS_SCORE_COUNT) ? best_cnt : best_cnt - c0;
-    *omega = best_bits;
-    return best_cnt > 0 && score >= alpha;
+    const int need = (mode == CCS_SCORE_COUNT) ? alpha : alpha + c0;
+    *omega = 0ull;
+    if (d - c0 < need) return false;
+    if (fingerprint_max_count<DMAX>(w[0], w[1], w[2], w[3], d) < need) return false;
+    return exact_score_values<DMAX>(v, d, alpha, mode, omega);
 }
 
 // Fingerprint bound on the score: with F the largest multiplicity of a
@@ -235,6 +234,56 @@ __device__ __forceinline__ void load_record(const ProblemDev &P, int i, int (&js
         js[4 * q + 2] = v.z;
         js[4 * q + 3] = v.w;
     }
+}
+
+// Sum of v[j] over row i's CSR columns in ascending j, from +0.0, skipping
+// zero entries, by the whole warp.  The lanes fetch 8 x 32 consecutive
+// entries at a time (eight independent loads each, then eight gathers), and
+// the nonzero ones are added chunk by chunk in lane order, so the order of
+// the additions is exactly the sequential one.  Result valid in every lane.
+__device__ __forceinline__ double warp_ordered_row_sum(const int64_t *ptr, const int32_t *cols,
+                                                       const double *v, int i, int lane) {
+    constexpr int kU = 8;
+    double s = 0.0;
+    const int64_t b = __ldg(ptr + i), e = __ldg(ptr + i + 1);
+    for (int64_t p0 = b; p0 < e; p0 += 32 * kU) {
+        int c[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t p = p0 + 32 * u + lane;
+            c[u] = (p < e) ? __ldg(cols + p) : -1;
+        }
+        double vj[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) vj[u] = (c[u] >= 0) ? __ldcg(v + c[u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            unsigned nz = __ballot_sync(0xffffffffu, vj[u] != 0.0);
+            while (nz) {
+                const int src = __ffs(nz) - 1;
+                nz &= nz - 1;
+                s = __dadd_rn(s, __shfl_sync(0xffffffffu, vj[u], src));
+            }
+        }
+    }
+    return s;
+}
+
+// For the lanes whose row has more contributors than its slot record holds
+// (`over`), the row sum by the whole warp, one such row after another; 0.0
+// in the other lanes.  Every lane of the warp must call it.
+__device__ __forceinline__ double overflow_row_sums(const ProblemDev &P, bool over, int i,
+                                                   int lane) {
+    double mine = 0.0;
+    unsigned ov = __ballot_sync(0xffffffffu, over);
+    while (ov) {
+        const int src = __ffs(ov) - 1;
+        ov &= ov - 1;
+        const int row = __shfl_sync(0xffffffffu, i, src);
+        const double s = warp_ordered_row_sum(P.csr_ptr, P.csr_cols, P.x_hat, row, lane);
+        if (lane == src) mine = s;
+    }
+    return mine;
 }
 
 // r_i = y_i - (sum of the nonzero x_hat_j, j in N(i), in ascending j, from

@@ -43,6 +43,7 @@ constexpr int kMaxBlocks = 1024;
 constexpr int kMaxProblems = 4096;  // per launch: their status and weight prefix live on chip
 constexpr int kMaxStampIters = 1024;
 constexpr int kMaxStages = 6;
+constexpr int kOvfCap = 512;       // overflow rows listed per CTA and segment
 constexpr int kQueueCap = 2048;     // most candidate columns queued per CTA and segment
 constexpr int kMinQueue = 256;      // fewest (more go through the inline exact path)
 constexpr int kFlagSkipArrive = 1;  // test hook: CTA 0 never arrives at barrier 1
@@ -327,14 +328,14 @@ __device__ __forceinline__ void issue_chunk(const EngineArgs &a, const ProblemDe
 // Exact score and apply of one column inside the stream (problems without
 // shared-memory fingerprints, or a full queue); the rows are read again from
 // global memory, so the stream loop keeps no copy of them.
-template <int DMAX>
+template <int DMAX, bool kPrefilter>
 __device__ __forceinline__ bool score_inline(const EngineArgs &a, const ProblemDev &P, int j) {
     const int d = P.d;
     int32_t rows[DMAX];
 #pragma unroll
     for (int t = 0; t < DMAX; ++t) rows[t] = (t < d) ? __ldg(P.csc_rows + (size_t)j * d + t) : 0;
     unsigned long long omega;
-    const bool acc = exact_score<DMAX>(rows, d, P.r, a.alpha, a.mode, &omega);
+    const bool acc = exact_score<DMAX, kPrefilter>(rows, d, P.r, a.alpha, a.mode, &omega);
     if (acc) apply_pair<DMAX>(P, j, rows, d, omega);
     return acc;
 }
@@ -467,7 +468,10 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
                             }
                         }
                     }
-                    if (inline_exact) acc = score_inline<DMAX>(a, P, j);
+                    // the 1024-thread instance (64 registers) serves only
+                    // problems with shared-memory fingerprints, whose
+                    // columns reach this point after the fingerprint test
+                    if (inline_exact) acc = score_inline<DMAX, THREADS != 1024>(a, P, j);
                 }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, acc);
@@ -496,24 +500,58 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
 // One row of the residual phase.  The touched flag, the row's slot record,
 // y_i and the old r_i are independent loads issued together; only touched
 // rows then gather their contributors' x_hat_j.
-__device__ __noinline__ long long residual_tile(const ProblemDev &P, int tile, int lane) {
+// One row tile of the residual phase.  Rows with more contributors than
+// their slot record holds are appended to the CTA's overflow list (summed
+// afterwards, one warp a row); when the list is full the warp sums them
+// itself.
+__device__ __noinline__ long long residual_tile(const ProblemDev &P, int tile, int lane,
+                                                int *ovf, int *ovf_n, int ovf_cap) {
     const int i = tile * kTile + lane;
     long long delta = 0;
+    bool touched = false, over = false;
+    int js[kSlotRec];
+    double yi = 0.0, ro = 0.0, s = 0.0;
     if (i < P.m) {
-        const uint8_t touched = __ldcg(P.touched + i);
-        int js[kSlotRec];
+        touched = __ldcg(P.touched + i) != 0;
         load_record(P, i, js);
-        const double yi = __ldg(P.y + i);
-        const double ro = __ldcg(P.r + i);
-        if (touched) {
-            P.touched[i] = 0;
-            const double rn = __dsub_rn(yi, row_sum_from_record(P, i, js));
-            delta = (long long)(rn != 0.0) - (long long)(ro != 0.0);
-            P.r[i] = rn;
-            P.fp[i] = fingerprint(rn);
+        yi = __ldg(P.y + i);
+        ro = __ldcg(P.r + i);
+        over = touched && js[0] > kSlots;
+        if (touched && !over) s = row_sum_from_record(P, i, js);
+    }
+    bool later = false;
+    if (over) {
+        const int q = atomicAdd(ovf_n, 1);
+        if (q < ovf_cap) {
+            ovf[q] = i;
+            later = true;
         }
     }
+    const double so = overflow_row_sums(P, over && !later, i, lane);
+    if (touched && !later) {
+        if (over) s = so;
+        P.touched[i] = 0;
+        const double rn = __dsub_rn(yi, s);
+        delta = (long long)(rn != 0.0) - (long long)(ro != 0.0);
+        P.r[i] = rn;
+        P.fp[i] = fingerprint(rn);
+    }
     return warp_sum_ll(delta);
+}
+
+// A listed overflow row, by one warp; returns the row's change of ||r||_0.
+__device__ __noinline__ long long residual_overflow_row(const ProblemDev &P, int i, int lane) {
+    const double s = warp_ordered_row_sum(P.csr_ptr, P.csr_cols, P.x_hat, i, lane);
+    long long delta = 0;
+    if (lane == 0) {
+        const double rn = __dsub_rn(__ldg(P.y + i), s);
+        const double ro = __ldcg(P.r + i);
+        delta = (long long)(rn != 0.0) - (long long)(ro != 0.0);
+        P.touched[i] = 0;
+        P.r[i] = rn;
+        P.fp[i] = fingerprint(rn);
+    }
+    return delta;
 }
 
 template <int DMAX, int THREADS>
@@ -524,6 +562,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
     __shared__ int s_qn;
     __shared__ unsigned long long s_acc;
     __shared__ long long s_sum;
+    __shared__ int s_ovf_n;
+    __shared__ int s_ovf[kOvfCap];  // rows whose sum needs the whole CSR row
     ScoreSmem S;
     S.fp = smem;
     S.stage = reinterpret_cast<char *>(smem + a.fp_cap);
@@ -687,10 +727,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
 
         // ---- residual + ||r||_0 ---------------------------------------------
         auto residual_segment = [&](const ProblemDev &P, int t0, int t1) {
-            if (threadIdx.x == 0) s_sum = 0;
+            if (threadIdx.x == 0) {
+                s_sum = 0;
+                s_ovf_n = 0;
+            }
             __syncthreads();
             for (int t = t0 + warp; t < t1; t += kWarps) {
-                const long long delta = residual_tile(P, t, lane);
+                const long long delta = residual_tile(P, t, lane, s_ovf, &s_ovf_n, kOvfCap);
+                if (lane == 0 && delta)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&s_sum), (unsigned long long)delta);
+            }
+            __syncthreads();
+            const int novf = min(s_ovf_n, kOvfCap);
+            for (int q = warp; q < novf; q += kWarps) {
+                const long long delta = residual_overflow_row(P, s_ovf[q], lane);
                 if (lane == 0 && delta)
                     atomicAdd(reinterpret_cast<unsigned long long *>(&s_sum), (unsigned long long)delta);
             }
@@ -903,7 +953,8 @@ static int plan_launch(ProblemDev *pds, int P, const ccs_params &prm, LaunchPlan
         set_last_error("csc_rows must be 16-byte aligned for the persistent engine");
         return CCS_EINVAL;
     }
-    const int sched = schedule_for(dmax, prm.schedule);
+    int sched = schedule_for(dmax, prm.schedule);
+    for (int attempt = 0; attempt < 2; ++attempt) {
     engine_fn fn = engine_kernel(dmax, sched);
     const int threads = sched == 1 ? 1024 : (sched == 3 ? 768 : 512);
     const int tpw = sched == 2 ? 2 : 1;  // kTpw of the kernel instance
@@ -938,6 +989,12 @@ static int plan_launch(ProblemDev *pds, int P, const ccs_params &prm, LaunchPlan
         if (pd.flags & kPdUseFp) fp_cap = std::max(fp_cap, need);
     }
     fp_cap = align_up(fp_cap, 128);
+    bool all_fp = true;
+    for (int p = 0; p < P; ++p) all_fp &= (pds[p].flags & kPdUseFp) != 0;
+    if (sched == 1 && !all_fp) {
+        sched = 3;  // problems without fingerprints need the exact-path prefilter
+        continue;
+    }
     const int stages =
         (int)std::min<size_t>(kMaxStages, (smem_limit - fixed - fp_cap) / stage_bytes);
     const size_t left = smem_limit - fp_cap - (size_t)stages * stage_bytes - status_bytes - 256;
@@ -965,6 +1022,9 @@ static int plan_launch(ProblemDev *pds, int P, const ccs_params &prm, LaunchPlan
     L.stage_bytes = stage_bytes;
     L.smem = smem;
     return CCS_OK;
+    }
+    set_last_error("no launch shape fits");
+    return CCS_EINVAL;
 }
 
 static void fill_args(EngineArgs &a, const LaunchPlan &L, int P, const ccs_params &prm) {
