@@ -69,6 +69,7 @@ static int decode_batch_impl(const ccs_problem *probs, int32_t count, const ccs_
         P.r = pr.r;
         P.r0_hist = pr.r0_hist;
         P.ctrl = header_ctrl(hdr, q);
+        P.out_slot = q;
         base += decode_ws_layout(pr.n, pr.m, &P, base);
     }
     if (capture) {
@@ -90,7 +91,31 @@ static int decode_batch_impl(const ccs_problem *probs, int32_t count, const ccs_
         }
         return CCS_OK;
     }
-    return engine_run(pds.data(), count, p, out, hdr, s, dev_out);
+    // Problems with d <= 8 and d > 8 run on different kernel instances (the
+    // register-resident arrays are sized by the largest d of a launch), so a
+    // mixed batch goes out as two launches, one per class, each over the
+    // whole GPU.  Every problem's result is the same either way.
+    std::vector<int> group[2];
+    for (int32_t q = 0; q < count; ++q) group[pds[q].d > 8].push_back(q);
+    if (group[0].empty() || group[1].empty())
+        return engine_run(pds.data(), count, p, out, hdr, s, dev_out);
+    std::vector<ProblemDev> sub;
+    std::vector<ccs_result> part;
+    for (const std::vector<int> &g : group) {
+        sub.clear();
+        for (int q : g) {
+            sub.push_back(pds[q]);
+            // the launch's control blocks sit at the front of the header;
+            // out_slot keeps the caller's index for device-side results
+            sub.back().ctrl = header_ctrl(hdr, (int)sub.size() - 1);
+        }
+        part.assign(sub.size(), ccs_result{});
+        rc = engine_run(sub.data(), (int)sub.size(), p, part.data(), hdr, s, dev_out);
+        if (rc != CCS_OK) return rc;
+        if (!dev_out)
+            for (size_t t = 0; t < g.size(); ++t) out[g[t]] = part[t];
+    }
+    return CCS_OK;
 }
 
 extern "C" int ccs_decode_batch(const ccs_problem *probs, int32_t count, const ccs_params *params,

@@ -195,14 +195,14 @@ __device__ __forceinline__ const ProblemDev &problem(const EngineArgs &a, int p)
 // A CTA that leaves early (a wait ran out) marks every device-side result.
 __device__ __forceinline__ void fail_out(const EngineArgs &a) {
     if (a.dev_out && threadIdx.x == 0)
-        for (int p = 0; p < a.P; ++p) a.dev_out[p].error = CCS_ETIMEOUT;
+        for (int p = 0; p < a.P; ++p) a.dev_out[problem(a, p).out_slot].error = CCS_ETIMEOUT;
 }
 
 // ---- work partition -----------------------------------------------------
 //
 // Every phase splits the tiles of the problems that are still running into
-// gridDim.x contiguous shares of equal weight.  A tile of problem p weighs
-// d_p for the score phase (its columns' row indices) and 1 for row tiles.
+// gridDim.x contiguous shares of equal weight (part_weight below gives a
+// tile's weight).
 // Each CTA computes the same prefix of weights over the problems in shared
 // memory and takes the tiles whose starting weight falls in its share, so
 // the shares follow the running set from one iteration to the next.
@@ -214,8 +214,12 @@ __device__ __forceinline__ long long part_tiles(const ProblemDev &P, int kind) {
                                                          : (P.m + kTile - 1) / kTile;
 }
 
+// Score tiles weigh d (their columns' row indices), four times more when the
+// problem's fingerprints are not in shared memory (every column then gathers
+// its d values of r); row tiles weigh 1.
 __device__ __forceinline__ long long part_weight(const ProblemDev &P, int kind) {
-    return kind == kPartScore ? P.d : 1;
+    if (kind != kPartScore) return 1;
+    return (P.flags & kPdUseFp) ? P.d : 4 * P.d;
 }
 
 // Does problem P take part in a partition of this kind?  Iteration phases:
@@ -793,7 +797,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
             res.r0_final = __ldcg(&P.ctrl->r0);
             res.error = __ldcg(&a.sync->error) ? CCS_ETIMEOUT : CCS_OK;
             res.reserved = 0;
-            a.dev_out[p] = res;
+            a.dev_out[P.out_slot] = res;
         }
     }
 }

@@ -43,6 +43,8 @@ struct ProblemDev {
     int n, m, d;
     int flags;            // kPdUseFp: fingerprints fit shared memory (engine);
                           // kPdFresh: initialise before iterating (resume mode)
+    int out_slot;         // index of this problem's entry in the engine's
+                          // device-side result array
     const int32_t *csc_rows;
     const int64_t *csr_ptr;
     const int32_t *csr_cols;

@@ -172,6 +172,7 @@ static void worker_loop(ccs_server *S) {
             D.ctrl = reinterpret_cast<DecodeCtrl *>(base);
             decode_ws_layout(D.n, D.m, &D, base + align_up(sizeof(DecodeCtrl), 256));
             D.flags = R.fresh ? kPdFresh : 0;
+            D.out_slot = p;
             if (R.fresh && cudaMemsetAsync(D.ctrl, 0, sizeof(DecodeCtrl), S->stream) != cudaSuccess)
                 rc = CCS_ECUDA;
         }
