@@ -77,9 +77,21 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+KERNEL_SOURCES = ("ccs_engine.cu", "ccs_device.cuh", "ccs_internal.cuh")
+
+
+def kernel_source_sha() -> str:
+    """Hash of the sources the persistent engine is compiled from."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1508_01256_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_record(kernel: str, workload_name: str):
     """Per-launch DRAM bytes from a committed ncu summary, if it was taken on
-    the current kernel source; else None."""
+    the current kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -89,9 +101,8 @@ def traffic_record(kernel: str, workload_name: str):
     entry = rec.get(kernel, {}).get(workload_name)
     if not entry:
         return None
-    src = os.path.join(ROOT, "paper_1508_01256_gb300", "csrc", entry["source"])
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = kernel_source_sha()
     except OSError:
         return None
     return entry["bytes_per_launch"] if sha == entry.get("source_sha") else None

@@ -72,14 +72,11 @@ static int decode_batch_impl(const ccs_problem *probs, int32_t count, const ccs_
         P.out_slot = q;
         base += decode_ws_layout(pr.n, pr.m, &P, base);
     }
-    if (capture) {
-        if (p.engine == CCS_ENGINE_HOST_LOOP) {
+    if (p.engine == CCS_ENGINE_HOST_LOOP) {
+        if (capture) {
             set_last_error("ccs_batch_graph_create: the host-driven engine cannot be captured");
             return CCS_EINVAL;
         }
-        return engine_capture(pds.data(), count, p, hdr, dev_out, capture);
-    }
-    if (p.engine == CCS_ENGINE_HOST_LOOP) {
         if (dev_out) {
             set_last_error("ccs_decode_batch_async: the host-driven engine cannot run asynchronously");
             return CCS_EINVAL;
@@ -95,26 +92,32 @@ static int decode_batch_impl(const ccs_problem *probs, int32_t count, const ccs_
     // register-resident arrays are sized by the largest d of a launch), so a
     // mixed batch goes out as two launches, one per class, each over the
     // whole GPU.  Every problem's result is the same either way.
-    std::vector<int> group[2];
-    for (int32_t q = 0; q < count; ++q) group[pds[q].d > 8].push_back(q);
-    if (group[0].empty() || group[1].empty())
-        return engine_run(pds.data(), count, p, out, hdr, s, dev_out);
-    std::vector<ProblemDev> sub;
-    std::vector<ccs_result> part;
-    for (const std::vector<int> &g : group) {
-        sub.clear();
-        for (int q : g) {
-            sub.push_back(pds[q]);
-            // the launch's control blocks sit at the front of the header;
-            // out_slot keeps the caller's index for device-side results
-            sub.back().ctrl = header_ctrl(hdr, (int)sub.size() - 1);
+    std::vector<int> order;
+    int sizes[2] = {0, 0};
+    for (int cls = 0; cls < 2; ++cls)
+        for (int32_t q = 0; q < count; ++q)
+            if ((pds[q].d > 8) == (cls == 1)) {
+                order.push_back(q);
+                ++sizes[cls];
+            }
+    const int groups = (sizes[0] && sizes[1]) ? 2 : 1;
+    if (groups == 1) sizes[0] = count;
+    // descriptors in launch order; each launch's control blocks sit at the
+    // front of the header, and out_slot keeps the caller's index
+    std::vector<ProblemDev> sub(count);
+    for (int g = 0, t = 0; g < groups; ++g)
+        for (int u = 0; u < sizes[g]; ++u, ++t) {
+            sub[t] = pds[order[t]];
+            sub[t].ctrl = header_ctrl(hdr, u);
         }
-        part.assign(sub.size(), ccs_result{});
-        rc = engine_run(sub.data(), (int)sub.size(), p, part.data(), hdr, s, dev_out);
+    if (capture) return engine_capture(sub.data(), sizes, groups, p, hdr, dev_out, capture);
+    std::vector<ccs_result> part(count);
+    for (int g = 0, first = 0; g < groups; first += sizes[g], ++g) {
+        rc = engine_run(sub.data() + first, sizes[g], p, part.data() + first, hdr, s, dev_out);
         if (rc != CCS_OK) return rc;
-        if (!dev_out)
-            for (size_t t = 0; t < g.size(); ++t) out[g[t]] = part[t];
     }
+    if (!dev_out)
+        for (int t = 0; t < count; ++t) out[order[t]] = part[t];
     return CCS_OK;
 }
 

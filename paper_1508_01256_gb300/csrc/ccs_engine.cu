@@ -1144,38 +1144,54 @@ int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, c
     return CCS_OK;
 }
 
-// Capture one decode launch (header memset + cooperative kernel) into a CUDA
-// graph.  The descriptors are uploaded now, outside the capture; the graph
-// bakes the workspace and array pointers.  Results go to dev_out.
-int engine_capture(ProblemDev *pds, int P, const ccs_params &prm, char *ws, ccs_result *dev_out,
-                   cudaGraphExec_t *exec) {
-    LaunchPlan L;
-    int rc = plan_launch(pds, P, prm, L);
-    if (rc) return rc;
-    EngineArgs a;
-    fill_args(a, L, P, prm);
-    a.sync = reinterpret_cast<EngineSync *>(ws);
-    a.dev_out = dev_out;
-    a.stamps = nullptr;
-    if (P == 1) {
-        a.single = pds[0];
-        a.probs = nullptr;
-    } else {
-        ProblemDev *d_probs = reinterpret_cast<ProblemDev *>(ws + sync_bytes(P) + stamps_bytes());
-        CCS_CUDA_TRY(cudaMemcpy(d_probs, pds, sizeof(ProblemDev) * P, cudaMemcpyHostToDevice));
-        a.probs = d_probs;
+// Capture decode launches (header memset + cooperative kernel, one pair per
+// group, run one after the other) into a CUDA graph.  pds holds the groups'
+// descriptors back to back, group g's sizes[g] of them, each with its control
+// block at the group's own index in the header.  The descriptors are uploaded
+// now, outside the capture, to disjoint places of the header; the graph bakes
+// the workspace and array pointers.  Results go to dev_out.
+int engine_capture(ProblemDev *pds, const int *sizes, int groups, const ccs_params &prm, char *ws,
+                   ccs_result *dev_out, cudaGraphExec_t *exec) {
+    int total = 0;
+    for (int g = 0; g < groups; ++g) total += sizes[g];
+    std::vector<EngineArgs> args(groups);
+    std::vector<LaunchPlan> plans(groups);
+    ProblemDev *d_probs = reinterpret_cast<ProblemDev *>(ws + sync_bytes(total) + stamps_bytes());
+    for (int g = 0, first = 0; g < groups; first += sizes[g], ++g) {
+        const int P = sizes[g];
+        int rc = plan_launch(pds + first, P, prm, plans[g]);
+        if (rc) return rc;
+        EngineArgs &a = args[g];
+        fill_args(a, plans[g], P, prm);
+        a.sync = reinterpret_cast<EngineSync *>(ws);
+        a.dev_out = dev_out;
+        a.stamps = nullptr;
+        if (P == 1) {
+            a.single = pds[first];
+            a.probs = nullptr;
+        } else {
+            a.probs = d_probs + first;
+        }
     }
+    // upload the descriptors with the flags plan_launch set
+    if (total > 1)
+        CCS_CUDA_TRY(cudaMemcpy(d_probs, pds, sizeof(ProblemDev) * total, cudaMemcpyHostToDevice));
     cudaStream_t cs;
     CCS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        void *args[] = {&a};
-        cudaError_t e1 = cudaMemsetAsync(ws, 0, sync_bytes(P), cs);
-        cudaError_t e2 = cudaLaunchCooperativeKernel((const void *)L.fn, dim3(L.G), dim3(L.threads),
-                                                     args, L.smem, cs);
+        cudaError_t e1 = cudaSuccess;
+        for (int g = 0; g < groups && e1 == cudaSuccess; ++g) {
+            const LaunchPlan &L = plans[g];
+            void *kargs[] = {&args[g]};
+            e1 = cudaMemsetAsync(ws, 0, sync_bytes(sizes[g]), cs);
+            if (e1 == cudaSuccess)
+                e1 = cudaLaunchCooperativeKernel((const void *)L.fn, dim3(L.G), dim3(L.threads),
+                                                 kargs, L.smem, cs);
+        }
         e = cudaStreamEndCapture(cs, &graph);
-        if (e == cudaSuccess) e = (e1 != cudaSuccess) ? e1 : e2;
+        if (e == cudaSuccess) e = e1;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);

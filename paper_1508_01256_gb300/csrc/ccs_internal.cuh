@@ -156,8 +156,10 @@ int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, c
 // iter_budget iterations run; out[p].status is -1 for problems still
 // running.  `hdr` needs engine_resume_header_bytes(P) bytes.
 size_t engine_resume_header_bytes(int P);
-int engine_capture(ProblemDev *pds, int P, const ccs_params &prm, char *ws, ccs_result *dev_out,
-                   cudaGraphExec_t *exec);
+// Graph of `groups` launches run in turn; pds holds group g's sizes[g]
+// descriptors after those of the groups before it.
+int engine_capture(ProblemDev *pds, const int *sizes, int groups, const ccs_params &prm, char *ws,
+                   ccs_result *dev_out, cudaGraphExec_t *exec);
 int engine_resume(ProblemDev *pds, int P, const ccs_params &prm, int iter_budget, ccs_result *out,
                   char *hdr, cudaStream_t s);
 int check_params(const ccs_params *p, int d);

@@ -351,6 +351,8 @@ def test_async_decode_matches_blocking(ccs, orc):
 def test_async_batch_matches_oracle(ccs, orc):
     import torch
     probs = inputs.batch_problems(16, seed=91, log2n_hi=15.0)
+    # both d classes: two launches, results written to interleaved slots
+    assert {p.d > 8 for p in probs} == {True, False}
     items = [device_problem(ccs, p) for p in probs]
     pbs, outs = [], []
     for (csc, ptr, cols, y), p in zip(items, probs):
@@ -389,6 +391,7 @@ def test_batch_graph_replays(ccs, orc):
     decodes the new signals (each against the oracle)."""
     import torch
     probs = inputs.batch_problems(10, seed=123, log2n_hi=15.0)
+    assert {p.d > 8 for p in probs} == {True, False}  # a graph of two launches
     items = [device_problem(ccs, p) for p in probs]
     outs, pbs = [], []
     for (csc, ptr, cols, y), p in zip(items, probs):
