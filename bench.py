@@ -244,6 +244,67 @@ def cpu_baseline(name: str, budget_s: float = 12.0):
             "exact_recovery": exact}
 
 
+def undersampling_sweep(ccs, dev, reps: int, peak: float, seed: int):
+    """n/m ~ 10^3 (Sec. 5.5 shape): n=2^24, m=16777, d=9, rho = 0.05..0.30 in
+    six steps on gauss-grid values, the +/-1 (non-dissociated) variant at
+    rho=0.05, and d=7, rho=0.05 beside the paper's Table 3 time.  Each point:
+    one untimed decode, then `reps` decodes with an L2 flush before each,
+    timed with CUDA events on the launching stream.  The CSC alone (604 MB at
+    d=9) is far larger than L2, so every iteration streams it from HBM."""
+    import numpy as np
+    import torch
+
+    from paper_1508_01256_gb300 import inputs
+    points = [(9, rho, "gauss-grid") for rho in (0.05, 0.10, 0.15, 0.20, 0.25, 0.30)]
+    points += [(9, 0.05, "pm1"), (7, 0.05, "gauss-grid")]
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    names = {ccs.CONVERGED: "converged", ccs.STALLED: "stalled", ccs.MAX_ITER: "max_iter"}
+    out = []
+    for i, (d, rho, model) in enumerate(points):
+        p = inputs.extreme_undersampling(rho, d=d, seed=seed + i, model=model)
+        csc, ptr, cols = ccs.make_expander(p.n, p.m, p.d, p.a_seed, device=dev)
+        y = ccs.measure(ptr, cols, torch.from_numpy(p.x).to(dev), p.m, p.d)
+        ws = ccs.workspace(ccs.ccs_workspace_size(ccs.OP_DECODE, p.n, p.m, p.d), dev)
+        x_hat = torch.empty(p.n, dtype=torch.float64, device=dev)
+        r = torch.empty(p.m, dtype=torch.float64, device=dev)
+        prm = ccs.params()
+        res_dev = ccs.result_buffer(reps + 1, dev)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(reps)]
+        for t in range(reps + 1):
+            flush.zero_()
+            if t > 0:
+                evs[t - 1][0].record(stream)
+            ccs.ccs_decode_parallel_l0_async(p.n, p.m, p.d, csc, ptr, cols, y, x_hat, r, None,
+                                             prm, res_dev[t * ccs.RESULT_BYTES:], ws, stream)
+            if t > 0:
+                evs[t - 1][1].record(stream)
+        torch.cuda.synchronize()
+        res = ccs.results_from_device(res_dev, reps + 1)
+        ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        last = res[-1]
+        it = last.iterations
+        alg = it * (4 * p.d * p.n + 8 * p.m)
+        gbs = alg / (ms * 1e-3) / 1e9
+        entry = {"n": p.n, "m": p.m, "d": p.d, "k": p.k, "rho": rho, "values": p.model,
+                 "ms_per_decode": ms, "decodes_per_s": 1000.0 / ms, "iterations": it,
+                 "status": names.get(last.status, last.status),
+                 "exact_recovery": bool(last.status == ccs.CONVERGED and
+                                        np.array_equal(x_hat.cpu().numpy(), p.x)),
+                 "same_every_rep": all((q.status, q.iterations, q.r0_final) ==
+                                       (res[0].status, res[0].iterations, res[0].r0_final)
+                                       for q in res),
+                 "algorithmic_bytes": alg, "achieved_gbs": gbs, "frac": gbs / peak,
+                 "column_updates_per_s": p.n * it / (ms * 1e-3)}
+        if d == 7 and rho == 0.05:
+            entry["paper_table3_s_k40"] = TABLE3_SECONDS[24]
+        out.append(entry)
+        del csc, ptr, cols, y, ws, x_hat, r
+        torch.cuda.empty_cache()
+    return {"reps": reps, "l2": "flushed before every decode (512 MB write)", "points": out}
+
+
 def batched_vs_plain(ccs, dev, count: int, seed: int, reps: int = 3):
     """Decodes/s of `count` mixed problems (n log-uniform in [2^12, 2^20],
     delta, rho, d drawn from the batched workload's sets) in ONE persistent
@@ -572,6 +633,10 @@ def run_ccs(args):
     serving = None
     if args.serve > 0:
         serving = serving_run(ccs, dev, args.serve, seed=1000 * rank + 777)
+    sweep = None
+    if args.undersampling > 0:
+        sweep = undersampling_sweep(ccs, dev, args.undersampling, measured_peaks()[0],
+                                    seed=1000 * rank + 20151508)
 
     if rank == 0:
         cb = None
@@ -598,6 +663,7 @@ def run_ccs(args):
                 "kernel_times": kernel_share,
                 "batched": batched,
                 "serving": serving,
+                "undersampling": sweep,
                 "wall_s_timed_region": wall}
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -621,6 +687,8 @@ def main():
                     help="problems in the batched-vs-plain comparison (0: skip)")
     ap.add_argument("--serve", type=int, default=256,
                     help="requests in the serving run (0: skip)")
+    ap.add_argument("--undersampling", type=int, default=3,
+                    help="timed decodes per point of the n/m ~ 10^3 sweep (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
