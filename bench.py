@@ -77,7 +77,7 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-KERNEL_SOURCES = ("ccs_engine.cu", "ccs_device.cuh", "ccs_internal.cuh")
+KERNEL_SOURCES = ("ccs_engine_kernel.cuh", "ccs_engine.cu", "ccs_device.cuh", "ccs_internal.cuh")
 
 
 def kernel_source_sha() -> str:

@@ -33,7 +33,7 @@ __global__ void k_init(ProblemDev P) {
     for (long long i = tid; i < P.m; i += stride) {
         const double v = P.y[i];
         P.r[i] = v;
-        P.fp[i] = fingerprint(v);
+        store_fp(P, i, v);
         P.touched[i] = 0;
         P.slots[(size_t)i * kSlotRec] = 0;
         nz += (v != 0.0);
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) k_residual(ProblemDev P) {
         const double ro = P.r[i];
         delta = (long long)(rn != 0.0) - (long long)(ro != 0.0);
         P.r[i] = rn;
-        P.fp[i] = fingerprint(rn);
+        store_fp(P, i, rn);
     }
     __shared__ long long s_delta;
     if (threadIdx.x == 0) s_delta = 0;

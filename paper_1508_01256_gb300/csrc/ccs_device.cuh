@@ -24,6 +24,22 @@ __device__ __forceinline__ uint8_t fingerprint_of_bits(unsigned long long b) {
 
 __device__ __forceinline__ uint8_t fingerprint(double v) { return fingerprint_of_bits(value_bits(v)); }
 
+// 16-bit fingerprint, same rule: 0 exactly for zero, else a hash in 1..65535.
+__device__ __forceinline__ uint16_t fingerprint16_of_bits(unsigned long long b) {
+    if (b == 0ull) return 0;
+    unsigned long long h = (b ^ (b >> 31)) * 0x9e3779b97f4a7c15ull;
+    const unsigned f = (unsigned)(h >> 48);
+    return (uint16_t)(f == 0u ? 1u : f);
+}
+
+// Store r_i's fingerprint in the problem's width.
+__device__ __forceinline__ void store_fp(const ProblemDev &P, int i, double v) {
+    if (fp16_for(P.m))
+        reinterpret_cast<uint16_t *>(P.fp)[i] = fingerprint16_of_bits(value_bits(v));
+    else
+        P.fp[i] = fingerprint(v);
+}
+
 // Largest multiplicity of a nonzero byte among the first d bytes of the
 // packed words w0..w3 (4 bytes each, position t in byte t%4 of word t/4),
 // counting each of the d(d-1)/2 pairs once.  Out of line, arguments in
@@ -51,6 +67,63 @@ __device__ __noinline__ int fingerprint_max_count(unsigned w0, unsigned w1, unsi
 #pragma unroll
     for (int t = 0; t < DMAX; ++t) F = (t < d && f[t] != 0u && cnt[t] > F) ? cnt[t] : F;
     return F;
+}
+
+// Largest multiplicity of a nonzero 16-bit value among the first d halves
+// of w0..w7 (position t in half t%2 of word t/2), as above.
+template <int DMAX>
+__device__ __noinline__ int fingerprint16_max_count(unsigned w0, unsigned w1, unsigned w2,
+                                                    unsigned w3, unsigned w4, unsigned w5,
+                                                    unsigned w6, unsigned w7, int d) {
+    const unsigned w[8] = {w0, w1, w2, w3, w4, w5, w6, w7};
+    unsigned f[DMAX];
+    int cnt[DMAX];
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t) {
+        f[t] = (w[t >> 1] >> (16 * (t & 1))) & 0xffffu;
+        cnt[t] = 1;
+    }
+#pragma unroll
+    for (int a = 0; a < DMAX; ++a)
+#pragma unroll
+        for (int b = a + 1; b < DMAX; ++b) {
+            const int e = (b < d) & (f[a] == f[b]);
+            cnt[a] += e;
+            cnt[b] += e;
+        }
+    int F = 0;
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t) F = (t < d && f[t] != 0u && cnt[t] > F) ? cnt[t] : F;
+    return F;
+}
+
+// Fingerprints of a column's rows packed for the pair count: kWide selects
+// 16-bit values (two a word) over 8-bit ones (four a word).
+template <int DMAX, bool kWide>
+struct FpWords {
+    static constexpr int kWords = kWide ? 8 : 4;
+    unsigned w[kWords];
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int q = 0; q < kWords; ++q) w[q] = 0u;
+    }
+    __device__ __forceinline__ void put(int t, unsigned f) {
+        if constexpr (kWide) w[t >> 1] |= f << (16 * (t & 1));
+        else w[t >> 2] |= f << (8 * (t & 3));
+    }
+    __device__ __forceinline__ int max_count(int d) const {
+        if constexpr (kWide)
+            return fingerprint16_max_count<DMAX>(w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7], d);
+        else
+            return fingerprint_max_count<DMAX>(w[0], w[1], w[2], w[3], d);
+    }
+};
+
+// A row's fingerprint from the shared copy (8- or 16-bit entries).
+template <bool kWide>
+__device__ __forceinline__ unsigned fp_at(const uint8_t *fp_smem, int row) {
+    if constexpr (kWide) return reinterpret_cast<const uint16_t *>(fp_smem)[row];
+    else return fp_smem[row];
 }
 
 // Exact score from the d gathered values v (value_bits form) -- the
@@ -119,20 +192,21 @@ __device__ __forceinline__ bool exact_score(const int32_t *rows, int d, const do
 // <= F (Alg. 8).  Returns false when no pair of this column can reach alpha.
 // The cheap test (F <= number of nonzero rows) runs first; the pair counts
 // only for the columns that pass it.
-template <int DMAX>
+template <int DMAX, bool kWide>
 __device__ __forceinline__ bool may_accept(const uint8_t *fp_smem, const int32_t *rows, int d,
                                            int alpha, int mode) {
-    unsigned w[4] = {0u, 0u, 0u, 0u};
+    FpWords<DMAX, kWide> W;
+    W.clear();
     int c0 = 0;
 #pragma unroll
     for (int t = 0; t < DMAX; ++t) {
-        const unsigned f = (t < d) ? (unsigned)fp_smem[rows[t]] : 0u;
+        const unsigned f = (t < d) ? fp_at<kWide>(fp_smem, rows[t]) : 0u;
         c0 += (t < d) & (f == 0u);
-        w[t >> 2] |= f << (8 * (t & 3));
+        W.put(t, f);
     }
     const int need = (mode == CCS_SCORE_COUNT) ? alpha : alpha + c0;  // F must reach this
     if (d - c0 < need) return false;
-    return fingerprint_max_count<DMAX>(w[0], w[1], w[2], w[3], d) >= need;
+    return W.max_count(d) >= need;
 }
 
 // Enter column j in the slot records of its d rows: all d slot claims

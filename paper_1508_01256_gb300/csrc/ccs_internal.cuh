@@ -58,10 +58,21 @@ struct ProblemDev {
     int32_t *slots;       // m * kSlotRec: per row, one 64-byte record holding the
                           // number of columns entered and (up to kSlots of)
                           // those columns, unordered
-    uint8_t *fp;          // m: 8-bit fingerprint of r_i (0 iff r_i == 0)
+    uint8_t *fp;          // m fingerprints of r_i (0 iff r_i == 0): 16-bit when
+                          // fp16_for(m), else 8-bit
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Problems with at most kFp16MaxM rows keep 16-bit residual fingerprints
+// (2m bytes, 64 KB at most), the others 8-bit ones.  The width depends on m
+// alone, so every launch that reads or writes a problem's fingerprints
+// agrees on it (a served problem meets several launch plans).
+constexpr int kFp16MaxM = 32768;
+__host__ __device__ inline bool fp16_for(int m) { return m <= kFp16MaxM; }
+__host__ __device__ inline size_t fp_bytes(int m) {
+    return fp16_for(m) ? 2 * (size_t)m + 32 : (size_t)m + 16;
+}
 
 // Workspace carve-up of one problem's arrays (its control block lives in the
 // workspace header, see engine_header_bytes): returns bytes used from `base`.
@@ -75,7 +86,7 @@ __host__ inline size_t decode_ws_layout(int n, int m, ProblemDev *pd, char *base
     char *touched = take((size_t)m);
     char *in_slots = take((size_t)n);
     char *slots = take((size_t)m * kSlotRec * 4);
-    char *fp = take((size_t)m + 16);
+    char *fp = take(fp_bytes(m));
     if (pd) {
         pd->fp = reinterpret_cast<uint8_t *>(fp);
         pd->touched = reinterpret_cast<uint8_t *>(touched);

@@ -115,6 +115,30 @@ def test_decode_extreme_undersampling_full(ccs, orc):
     assert g.status == ccs.CONVERGED
 
 
+def test_decode_extreme_dense_residual_full(ccs, orc):
+    """n = 2^24, m = 16777, d = 9, rho = 0.30 (beyond recovery: r stays
+    dense, so most columns pass the zero-count part of the fingerprint bound
+    and many reach the exact score), first three iterations compared whole."""
+    p = inputs.extreme_undersampling(0.30, d=9, seed=8)
+    g, ref = _decode_both(ccs, orc, p, max_iter=3)
+    assert_same_decode(g, ref)
+    assert g.iterations == 3
+
+
+def test_batch_both_fingerprint_widths(ccs, orc):
+    """One batch with problems on both sides of the 16-bit fingerprint limit
+    (m <= 32768 keeps 16-bit fingerprints, larger m 8-bit ones), d <= 8 and
+    d > 8, each equal to the oracle."""
+    shapes = [(200000, 60000, 7, 3000), (50000, 5000, 7, 500), (100000, 40000, 9, 2000),
+              (30000, 3000, 9, 300), (70000, 32768, 5, 1600), (70000, 32769, 5, 1600)]
+    probs = [inputs.make_problem(*sh, seed=900 + i) for i, sh in enumerate(shapes)]
+    items = [device_problem(ccs, p) for p in probs]
+    outs = ccs.decode_batch(items, history=True)
+    for p, g in zip(probs, outs):
+        A, y_ref = oracle_problem(orc, p)
+        assert_same_decode(g, orc.parallel_l0(A, p.m, y_ref))
+
+
 def test_decode_extreme_pm1(ccs, orc):
     p = inputs.extreme_undersampling(0.05, d=9, seed=6, model="pm1", log2n=20)
     g, ref = _decode_both(ccs, orc, p)
