@@ -384,8 +384,12 @@ __device__ __forceinline__ void score_queue(const EngineArgs &a, const ProblemDe
 // kDenseLanes such lanes in a tile does not run the pair count there: it
 // appends the columns to its buffer and counts them 32 at a time, so the
 // pair count runs on full warps instead of once per tile that has a passing
-// lane.
+// lane.  The 1024-thread instance (64 registers a thread) keeps the in-place
+// test for 8-bit fingerprints: there the buffer path costs more in spills
+// than it saves (measured at n=2^20, m=2^17, d=7).
 constexpr int kDenseLanes = 12;
+template <int THREADS, bool kWide>
+constexpr bool kUseWarpBuffer = THREADS != 1024 || kWide;
 
 // Fingerprint pair test, then queue (or inline exact score), of up to 32
 // buffered columns (one per lane; their row indices are read again, from L2
@@ -483,7 +487,7 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
                 const bool pass = live && nz >= need;
                 const unsigned bal = __ballot_sync(0xffffffffu, pass);
                 if (bal) {
-                    if (__popc(bal) >= kDenseLanes) {
+                    if (!kUseWarpBuffer<THREADS, kWide> || __popc(bal) >= kDenseLanes) {
                         if (pass && W.max_count(d) >= need) {
                             const int q = atomicAdd(S.qn, 1);
                             if (q < a.queue_cap) {  // scored after the stream
@@ -495,7 +499,7 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
                                 acc = score_inline<DMAX, THREADS != 1024>(a, P, j);
                             }
                         }
-                    } else {
+                    } else if constexpr (kUseWarpBuffer<THREADS, kWide>) {
                         // append; a full buffer is tested right away and the
                         // lanes that did not fit start the next one
                         const int cnt = __popc(bal);
@@ -519,7 +523,7 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.empty[slot]);  // this warp is done with the stage
     }
-    if (wbn > 0 && ok) {
+    if (kUseWarpBuffer<THREADS, kWide> && wbn > 0 && ok) {
         __syncwarp();
         n_acc += flush_candidates<DMAX, THREADS, kExactD, kWide>(a, P, S.fp, wb, wbn, S.queue,
                                                                  S.qn);
