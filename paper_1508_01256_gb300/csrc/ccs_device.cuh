@@ -186,27 +186,32 @@ __device__ __forceinline__ bool exact_score(const int32_t *rows, int d, const do
     return exact_score_values<DMAX>(v, d, alpha, mode, omega);
 }
 
-// Fingerprint bound on the score: with F the largest multiplicity of a
-// nonzero fingerprint among the d rows and c0 the number of zero rows,
-// every value omega has c_omega <= F, so score <= F - c0 (Eq. (15)) or
-// <= F (Alg. 8).  Returns false when no pair of this column can reach alpha.
-// The cheap test (F <= number of nonzero rows) runs first; the pair counts
-// only for the columns that pass it.
+// Whether two of a column's nonzero fingerprints f[0..d) are equal.  Zero
+// entries and the positions beyond d are replaced by values no fingerprint
+// takes (above 16 bits, distinct per position), so one compare per pair
+// decides.  Every score needs at least alpha >= 2 equal nonzero values, so a
+// column without such a pair is rejected exactly.
+template <int DMAX>
+__device__ __forceinline__ bool fp_pair_exists(const unsigned (&f)[DMAX], int d) {
+    unsigned g[DMAX];
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t) g[t] = (t < d && f[t] != 0u) ? f[t] : (0x10000u + t);
+    bool any = false;
+#pragma unroll
+    for (int a = 0; a < DMAX; ++a)
+#pragma unroll
+        for (int b = a + 1; b < DMAX; ++b) any |= (g[a] == g[b]);
+    return any;
+}
+
+// Largest multiplicity of a nonzero fingerprint among f[0..d).
 template <int DMAX, bool kWide>
-__device__ __forceinline__ bool may_accept(const uint8_t *fp_smem, const int32_t *rows, int d,
-                                           int alpha, int mode) {
+__device__ __forceinline__ int fp_max_count(const unsigned (&f)[DMAX], int d) {
     FpWords<DMAX, kWide> W;
     W.clear();
-    int c0 = 0;
 #pragma unroll
-    for (int t = 0; t < DMAX; ++t) {
-        const unsigned f = (t < d) ? fp_at<kWide>(fp_smem, rows[t]) : 0u;
-        c0 += (t < d) & (f == 0u);
-        W.put(t, f);
-    }
-    const int need = (mode == CCS_SCORE_COUNT) ? alpha : alpha + c0;  // F must reach this
-    if (d - c0 < need) return false;
-    return W.max_count(d) >= need;
+    for (int t = 0; t < DMAX; ++t) W.put(t, f[t]);
+    return W.max_count(d);
 }
 
 // Enter column j in the slot records of its d rows: all d slot claims

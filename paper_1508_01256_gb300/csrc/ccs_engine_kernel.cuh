@@ -24,8 +24,10 @@
 //     stages so the next chunks are in flight while warps work on this one;
 //   - each warp tests its 32 columns against the fingerprint bound (a value's
 //     count never exceeds its fingerprint's count), from shared memory only:
-//     first the zero count, then (for the columns that pass it, gathered 32
-//     at a time in a per-warp buffer when they are few) the pair count;
+//     first the zero count, then whether any two nonzero fingerprints are
+//     equal, and the full count only when the score needs three or more
+//     (columns that pass the zero count are gathered 32 at a time in a
+//     per-warp buffer when a tile has few of them);
 //   - the few columns that may reach alpha are queued, then scored exactly,
 //     lane-parallel across the CTA: d binary64 gathers of r each.
 // Problems whose fingerprints do not fit shared memory score every column
@@ -379,44 +381,67 @@ __device__ __forceinline__ void score_queue(const EngineArgs &a, const ProblemDe
     }
 }
 
-// Columns whose zero count alone leaves room for a pair (the cheap part of
-// the fingerprint bound) are rare once r is sparse.  A warp with fewer than
-// kDenseLanes such lanes in a tile does not run the pair count there: it
-// appends the columns to its buffer and counts them 32 at a time, so the
-// pair count runs on full warps instead of once per tile that has a passing
-// lane.  The 1024-thread instance (64 registers a thread) keeps the in-place
-// test for 8-bit fingerprints: there the buffer path costs more in spills
-// than it saves (measured at n=2^20, m=2^17, d=7).
+// Once r is sparse few columns pass the zero count.  A warp with fewer than
+// kDenseLanes such lanes in a tile does not test them there: it appends them
+// to its buffer and tests them 32 at a time, so the rest of the test runs on
+// full warps instead of once per tile that has a passing lane.  The
+// 1024-thread instance (64 registers a thread) always tests in place: there
+// the buffer path costs more in spills than it saves (measured at n=2^20,
+// m=2^17 and at n=2^24, m=16777, both d=7; at d=9 on 512 threads it saves 5 %).
 constexpr int kDenseLanes = 12;
 template <int THREADS, bool kWide>
-constexpr bool kUseWarpBuffer = THREADS != 1024 || kWide;
+constexpr bool kUseWarpBuffer = THREADS != 1024;
 
-// Fingerprint pair test, then queue (or inline exact score), of up to 32
+// The rest of the fingerprint bound for a column that passed the zero count
+// (its fingerprints f, nz of them nonzero): a nonzero pair, then, only when
+// the score needs three or more equal values, the full count.
+template <int DMAX, bool kWide>
+__device__ __forceinline__ bool fp_bound_passes(const unsigned (&f)[DMAX], int d, int need) {
+    if (!fp_pair_exists<DMAX>(f, d)) return false;
+    return need <= 2 || fp_max_count<DMAX, kWide>(f, d) >= need;
+}
+
+// Queue column j (rows in `rows`) for the exact score, or score it inline
+// when the queue is full; returns whether it was accepted inline.
+template <int DMAX, int THREADS>
+__device__ __forceinline__ bool queue_or_score(const EngineArgs &a, const ProblemDev &P,
+                                               int32_t *queue, int *qn, int j,
+                                               const int32_t (&rows)[DMAX]) {
+    const int q = atomicAdd(qn, 1);
+    if (q < a.queue_cap) {  // scored after the stream
+        int32_t *e = queue + q * (DMAX + 1);
+        e[0] = j;
+#pragma unroll
+        for (int t = 0; t < DMAX; ++t) e[1 + t] = rows[t];
+        return false;
+    }
+    return score_inline<DMAX, THREADS != 1024>(a, P, j);
+}
+
+// The fingerprint test, then queue (or inline exact score), of up to 32
 // buffered columns (one per lane; their row indices are read again, from L2
 // shortly after the stream brought them).  Returns the number accepted inline.
 template <int DMAX, int THREADS, bool kExactD, bool kWide>
 __device__ __noinline__ int flush_candidates(const EngineArgs &a, const ProblemDev &P,
-                                             const uint8_t *fp, const int *wb, int cnt,
-                                             int32_t *queue, int *qn) {
+                                             const uint8_t *fp, int32_t *queue, int *qn,
+                                             const int *wb, int cnt) {
     const int lane = threadIdx.x & 31;
     const int d = kExactD ? DMAX : P.d;
     bool acc = false;
     if (lane < cnt) {
         const int j = wb[lane];
         int32_t rows[DMAX];
+        unsigned f[DMAX];
+        int nz = 0;
 #pragma unroll
-        for (int t = 0; t < DMAX; ++t) rows[t] = (t < d) ? __ldg(P.csc_rows + (size_t)j * d + t) : 0;
-        if (may_accept<DMAX, kWide>(fp, rows, d, a.alpha, a.mode)) {
-            const int q = atomicAdd(qn, 1);
-            if (q < a.queue_cap) {
-                int32_t *e = queue + q * (DMAX + 1);
-                e[0] = j;
-#pragma unroll
-                for (int t = 0; t < DMAX; ++t) e[1 + t] = rows[t];
-            } else {
-                acc = score_inline<DMAX, THREADS != 1024>(a, P, j);
-            }
+        for (int t = 0; t < DMAX; ++t) {
+            rows[t] = (t < d) ? __ldg(P.csc_rows + (size_t)j * d + t) : 0;
+            f[t] = (t < d) ? fp_at<kWide>(fp, rows[t]) : 0u;
+            nz += (f[t] != 0u);
         }
+        const int need = (a.mode == CCS_SCORE_COUNT) ? a.alpha : a.alpha + (d - nz);
+        if (fp_bound_passes<DMAX, kWide>(f, d, need))
+            acc = queue_or_score<DMAX, THREADS>(a, P, queue, qn, j, rows);
     }
     return __popc(__ballot_sync(0xffffffffu, acc));
 }
@@ -473,32 +498,23 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
             if (!use_fp) {
                 if (live) acc = score_inline<DMAX, THREADS != 1024>(a, P, j);
             } else {
-                // cheap part of the bound: enough nonzero rows for the score
-                FpWords<DMAX, kWide> W;
-                W.clear();
+                // the fingerprint bound: enough nonzero rows for the score
+                // (zero count), then a nonzero pair, then, only when the
+                // score needs three or more equal values, the full count
+                unsigned f[DMAX];
                 int nz = 0;
 #pragma unroll
                 for (int t = 0; t < DMAX; ++t) {
-                    const unsigned f = (t < d) ? fp_at<kWide>(S.fp, rows[t]) : 0u;
-                    nz += (f != 0u);
-                    W.put(t, f);
+                    f[t] = (t < d) ? fp_at<kWide>(S.fp, rows[t]) : 0u;
+                    nz += (f[t] != 0u);
                 }
                 const int need = (a.mode == CCS_SCORE_COUNT) ? a.alpha : a.alpha + (d - nz);
                 const bool pass = live && nz >= need;
                 const unsigned bal = __ballot_sync(0xffffffffu, pass);
                 if (bal) {
                     if (!kUseWarpBuffer<THREADS, kWide> || __popc(bal) >= kDenseLanes) {
-                        if (pass && W.max_count(d) >= need) {
-                            const int q = atomicAdd(S.qn, 1);
-                            if (q < a.queue_cap) {  // scored after the stream
-                                int32_t *e = S.queue + q * (DMAX + 1);
-                                e[0] = j;
-#pragma unroll
-                                for (int t = 0; t < DMAX; ++t) e[1 + t] = rows[t];
-                            } else {
-                                acc = score_inline<DMAX, THREADS != 1024>(a, P, j);
-                            }
-                        }
+                        if (pass && fp_bound_passes<DMAX, kWide>(f, d, need))
+                            acc = queue_or_score<DMAX, THREADS>(a, P, S.queue, S.qn, j, rows);
                     } else if constexpr (kUseWarpBuffer<THREADS, kWide>) {
                         // append; a full buffer is tested right away and the
                         // lanes that did not fit start the next one
@@ -508,7 +524,7 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
                         if (wbn + cnt >= 32) {
                             __syncwarp();
                             n_acc += flush_candidates<DMAX, THREADS, kExactD, kWide>(
-                                a, P, S.fp, wb, 32, S.queue, S.qn);
+                                a, P, S.fp, S.queue, S.qn, wb, 32);
                             __syncwarp();
                             if (pass && slot_w >= 32) wb[slot_w - 32] = j;
                             wbn += cnt - 32;
@@ -525,8 +541,8 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
     }
     if (kUseWarpBuffer<THREADS, kWide> && wbn > 0 && ok) {
         __syncwarp();
-        n_acc += flush_candidates<DMAX, THREADS, kExactD, kWide>(a, P, S.fp, wb, wbn, S.queue,
-                                                                 S.qn);
+        n_acc += flush_candidates<DMAX, THREADS, kExactD, kWide>(a, P, S.fp, S.queue, S.qn, wb,
+                                                                 wbn);
     }
     if (lane == 0 && n_acc) atomicAdd(S.acc, (unsigned long long)n_acc);
 }
