@@ -372,7 +372,13 @@ def batched_vs_plain(ccs, dev, count: int, seed: int, reps: int = 3):
                 for i, a in enumerate(rb))
     mb, mp, mg = statistics.median(tb), statistics.median(tp), statistics.median(tg)
     cols_total = sum(p.n * a.iterations for p, a in zip(probs, rb))
+    # aggregate roofline of the batched launch: every problem's algorithmic
+    # bytes, iterations x (4 d n + 8 m), over the batched time
+    alg = sum(a.iterations * (4 * p.d * p.n + 8 * p.m) for p, a in zip(probs, rb))
+    peak = measured_peaks()[0]
     return {"problems": count, "batched_decodes_per_s": count / (mb / 1000.0),
+            "algorithmic_bytes": alg, "achieved_gbs": alg / (mb * 1e-3) / 1e9,
+            "frac": alg / (mb * 1e-3) / 1e9 / peak,
             "plain_decodes_per_s": count / (mp / 1000.0), "batched_ms": mb, "plain_ms": mp,
             "graph_batched_decodes_per_s": count / (mg / 1000.0), "graph_ms": mg,
             "speedup": mp / mb, "batched_column_updates_per_s": cols_total / (mb / 1000.0),

@@ -98,7 +98,14 @@ typedef struct {
     int32_t debug_flags;  /* test hooks, 0 in normal use.  Bit 0 (persistent
                              engine): CTA 0 skips its arrival at the first
                              score barrier, so every CTA's bounded wait runs
-                             out and the call returns CCS_ETIMEOUT           */
+                             out and the call returns CCS_ETIMEOUT.  Bit 1:
+                             the persistent engine keeps the residual by
+                             ordered row sums from the first iteration
+                             instead of by exact atomic updates.  Bit 2: the
+                             test that certifies those updates exact is
+                             treated as failing from iteration 2, so the
+                             decode switches residual mode mid-way.  Results
+                             are the same for every setting of bits 1, 2.    */
     int32_t schedule;     /* persistent-engine launch shape: 0 = library's
                              choice (1 when d <= 8, else 2); 1 = 1024
                              threads a CTA, one 32-column tile per warp and

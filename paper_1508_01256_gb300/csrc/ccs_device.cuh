@@ -261,6 +261,34 @@ __device__ __forceinline__ void apply_pair_loaded(const ProblemDev &P, int j, co
     }
 }
 
+// Exponent e of the lowest set bit of a nonzero binary64 value given by its
+// bits b (|v| = k 2^e with k odd).
+__device__ __forceinline__ int lowbit_exponent(unsigned long long b) {
+    const int E = (int)((b >> 52) & 0x7ffull);
+    const unsigned long long M = b & 0xfffffffffffffull;
+    if (E == 0) return -1074 + __ffsll((long long)M) - 1;
+    return E - 1075 + __ffsll((long long)(M | (1ull << 52))) - 1;
+}
+
+// Apply an accepted pair while the problem's incremental residual is exact
+// (the persistent engine's certificate holds): x_hat_j <- x_hat_j + omega and
+// r_i <- r_i - omega on the column's d rows, as binary64 atomic adds into
+// r_next.  Every partial result is exact, so the order of the adds does not
+// matter and r_next ends equal to y - (ordered sum of the nonzero x_hat).
+// The new |x_hat_j| goes into the CTA's running maximum *xmax_s (bits).
+template <int DMAX>
+__device__ __forceinline__ void apply_exact(const ProblemDev &P, int j, const int32_t *rows, int d,
+                                            unsigned long long omega_bits, double xj,
+                                            unsigned long long *xmax_s) {
+    const double omega = __longlong_as_double((long long)omega_bits);
+    const double xn = __dadd_rn(xj, omega);
+    P.x_hat[j] = xn;
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t)
+        if (t < d) atomicAdd(P.r_next + rows[t], -omega);
+    atomicMax(xmax_s, value_bits(xn) & 0x7fffffffffffffffull);
+}
+
 // Ordered row sum from the row's 64-byte slot record js[0..kSlotRec)
 // (count, then the columns): the sum of the nonzero x_hat_j, j in N(i), in
 // ascending j, from +0.0.

@@ -178,7 +178,7 @@ static int plan_launch(ProblemDev *pds, int P, const ccs_params &prm, LaunchPlan
     const size_t stage_bytes = align_up((size_t)(warps - 1) * tpw * kTile * dmax * 4, 128);
     const size_t entry = (size_t)(dmax + 1) * 4;  // one queued candidate
     const size_t status_bytes = align_up((size_t)P, 16) + sizeof(long long) * (size_t)(P + 1) +
-                                sizeof(int) * (size_t)P;
+                                sizeof(int) * (size_t)P + (size_t)P;  // + residual modes
     if (P > kMaxProblems) {
         set_last_error("at most %d problems per launch (got %d)", kMaxProblems, P);
         return CCS_EINVAL;

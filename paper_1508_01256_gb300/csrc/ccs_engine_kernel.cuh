@@ -51,6 +51,8 @@ constexpr int kOvfCap = 512;       // overflow rows listed per CTA and segment
 constexpr int kQueueCap = 2048;     // most candidate columns queued per CTA and segment
 constexpr int kMinQueue = 256;      // fewest (more go through the inline exact path)
 constexpr int kFlagSkipArrive = 1;  // test hook: CTA 0 never arrives at barrier 1
+constexpr int kFlagOrdered = 2;     // test hook: ordered residual from the start
+constexpr int kFlagSwitch = 4;      // test hook: the certificate fails from iteration 2
 constexpr int kFpChunk = 32768;     // bytes per fingerprint bulk copy
 constexpr int kWbufPerWarp = 32;    // buffered candidate columns per consumer warp
 constexpr int kSubBase = 3 * kMaxStampIters + 2;  // CTA-0 score sub-phase stamps start here
@@ -311,6 +313,7 @@ struct ScoreSmem {
     int *qn;           // queue length
     unsigned long long *acc;  // accepted pairs of this CTA in the current segment
     int *wbuf;         // per consumer warp: kWbufPerWarp buffered candidate columns
+    unsigned long long *xmax;  // bits of the largest |x_hat_j| this CTA set (exact mode)
 };
 
 // Columns [col0, col1) of chunk `c` of a segment (tiles lo + c*W .. +W).
@@ -339,14 +342,18 @@ __device__ __forceinline__ void issue_chunk(const EngineArgs &a, const ProblemDe
 // shared-memory fingerprints, or a full queue); the rows are read again from
 // global memory, so the stream loop keeps no copy of them.
 template <int DMAX, bool kPrefilter>
-__device__ __forceinline__ bool score_inline(const EngineArgs &a, const ProblemDev &P, int j) {
+__device__ __forceinline__ bool score_inline(const EngineArgs &a, const ProblemDev &P, int j,
+                                             bool exact, unsigned long long *xmax_s) {
     const int d = P.d;
     int32_t rows[DMAX];
 #pragma unroll
     for (int t = 0; t < DMAX; ++t) rows[t] = (t < d) ? __ldg(P.csc_rows + (size_t)j * d + t) : 0;
     unsigned long long omega;
     const bool acc = exact_score<DMAX, kPrefilter>(rows, d, P.r, a.alpha, a.mode, &omega);
-    if (acc) apply_pair<DMAX>(P, j, rows, d, omega);
+    if (acc) {
+        if (exact) apply_exact<DMAX>(P, j, rows, d, omega, __ldcg(P.x_hat + j), xmax_s);
+        else apply_pair<DMAX>(P, j, rows, d, omega);
+    }
     return acc;
 }
 
@@ -355,7 +362,8 @@ __device__ __forceinline__ bool score_inline(const EngineArgs &a, const ProblemD
 template <int DMAX>
 __device__ __forceinline__ void score_queue(const EngineArgs &a, const ProblemDev &P,
                                          const int32_t *queue, int qn,
-                                         unsigned long long *acc_smem, bool ok) {
+                                         unsigned long long *acc_smem, bool ok, bool exact,
+                                         unsigned long long *xmax_s) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int d = P.d;
     for (int b0 = warp * 32; b0 < qn; b0 += blockDim.x) {
@@ -374,7 +382,10 @@ __device__ __forceinline__ void score_queue(const EngineArgs &a, const ProblemDe
             const uint8_t ins = __ldcg(P.in_slots + j);
             unsigned long long omega;
             acc = exact_score_values<DMAX>(v, d, a.alpha, a.mode, &omega);
-            if (acc) apply_pair_loaded<DMAX>(P, j, rows, d, omega, xj, ins);
+            if (acc) {
+                if (exact) apply_exact<DMAX>(P, j, rows, d, omega, xj, xmax_s);
+                else apply_pair_loaded<DMAX>(P, j, rows, d, omega, xj, ins);
+            }
         }
         const unsigned bal = __ballot_sync(0xffffffffu, acc);
         if (lane == 0 && bal) atomicAdd(acc_smem, (unsigned long long)__popc(bal));
@@ -406,7 +417,8 @@ __device__ __forceinline__ bool fp_bound_passes(const unsigned (&f)[DMAX], int d
 template <int DMAX, int THREADS>
 __device__ __forceinline__ bool queue_or_score(const EngineArgs &a, const ProblemDev &P,
                                                int32_t *queue, int *qn, int j,
-                                               const int32_t (&rows)[DMAX]) {
+                                               const int32_t (&rows)[DMAX], bool exact,
+                                               unsigned long long *xmax_s) {
     const int q = atomicAdd(qn, 1);
     if (q < a.queue_cap) {  // scored after the stream
         int32_t *e = queue + q * (DMAX + 1);
@@ -415,7 +427,7 @@ __device__ __forceinline__ bool queue_or_score(const EngineArgs &a, const Proble
         for (int t = 0; t < DMAX; ++t) e[1 + t] = rows[t];
         return false;
     }
-    return score_inline<DMAX, THREADS != 1024>(a, P, j);
+    return score_inline<DMAX, THREADS != 1024>(a, P, j, exact, xmax_s);
 }
 
 // The fingerprint test, then queue (or inline exact score), of up to 32
@@ -424,7 +436,8 @@ __device__ __forceinline__ bool queue_or_score(const EngineArgs &a, const Proble
 template <int DMAX, int THREADS, bool kExactD, bool kWide>
 __device__ __noinline__ int flush_candidates(const EngineArgs &a, const ProblemDev &P,
                                              const uint8_t *fp, int32_t *queue, int *qn,
-                                             const int *wb, int cnt) {
+                                             const int *wb, int cnt, bool exact,
+                                             unsigned long long *xmax_s) {
     const int lane = threadIdx.x & 31;
     const int d = kExactD ? DMAX : P.d;
     bool acc = false;
@@ -441,7 +454,7 @@ __device__ __noinline__ int flush_candidates(const EngineArgs &a, const ProblemD
         }
         const int need = (a.mode == CCS_SCORE_COUNT) ? a.alpha : a.alpha + (d - nz);
         if (fp_bound_passes<DMAX, kWide>(f, d, need))
-            acc = queue_or_score<DMAX, THREADS>(a, P, queue, qn, j, rows);
+            acc = queue_or_score<DMAX, THREADS>(a, P, queue, qn, j, rows, exact, xmax_s);
     }
     return __popc(__ballot_sync(0xffffffffu, acc));
 }
@@ -454,7 +467,7 @@ template <int DMAX, int THREADS, bool kExactD, bool kWide>
 __device__ __forceinline__ void consume_segment(const EngineArgs &a, const ProblemDev &P,
                                                 const Segment &sg, int per, int nchunks,
                                                 unsigned chunk_seq, ScoreSmem &S, int *wb,
-                                                bool &ok) {
+                                                bool exact, bool &ok) {
     constexpr int kTpw = (THREADS == 512) ? 2 : 1;
     const int warps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -496,7 +509,7 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
             }
             bool acc = false;
             if (!use_fp) {
-                if (live) acc = score_inline<DMAX, THREADS != 1024>(a, P, j);
+                if (live) acc = score_inline<DMAX, THREADS != 1024>(a, P, j, exact, S.xmax);
             } else {
                 // the fingerprint bound: enough nonzero rows for the score
                 // (zero count), then a nonzero pair, then, only when the
@@ -514,7 +527,8 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
                 if (bal) {
                     if (!kUseWarpBuffer<THREADS, kWide> || __popc(bal) >= kDenseLanes) {
                         if (pass && fp_bound_passes<DMAX, kWide>(f, d, need))
-                            acc = queue_or_score<DMAX, THREADS>(a, P, S.queue, S.qn, j, rows);
+                            acc = queue_or_score<DMAX, THREADS>(a, P, S.queue, S.qn, j, rows,
+                                                                exact, S.xmax);
                     } else if constexpr (kUseWarpBuffer<THREADS, kWide>) {
                         // append; a full buffer is tested right away and the
                         // lanes that did not fit start the next one
@@ -524,7 +538,7 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
                         if (wbn + cnt >= 32) {
                             __syncwarp();
                             n_acc += flush_candidates<DMAX, THREADS, kExactD, kWide>(
-                                a, P, S.fp, S.queue, S.qn, wb, 32);
+                                a, P, S.fp, S.queue, S.qn, wb, 32, exact, S.xmax);
                             __syncwarp();
                             if (pass && slot_w >= 32) wb[slot_w - 32] = j;
                             wbn += cnt - 32;
@@ -542,7 +556,7 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
     if (kUseWarpBuffer<THREADS, kWide> && wbn > 0 && ok) {
         __syncwarp();
         n_acc += flush_candidates<DMAX, THREADS, kExactD, kWide>(a, P, S.fp, S.queue, S.qn, wb,
-                                                                 wbn);
+                                                                 wbn, exact, S.xmax);
     }
     if (lane == 0 && n_acc) atomicAdd(S.acc, (unsigned long long)n_acc);
 }
@@ -552,10 +566,18 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
 // every consumer warp has released it.  Warps 1.. consume their tiles of
 // each chunk (consume_segment).  Then every warp scores the queued
 // candidates exactly.
+//
+// rmode: 0 while the problem's incremental residual is certified exact
+// (accepted pairs update r_next by atomic adds), 1 for the ordered residual
+// (contributor records), 2 in the iteration that switches from 0 to 1 (the
+// segment's nonzero columns enter their rows' records first).  it: the
+// problem's own iteration number.
 template <int DMAX, int THREADS>
 __device__ __forceinline__ void score_segment(const EngineArgs &a, const ProblemDev &P,
-                                              int seg_lo, int seg_hi, int g, ScoreSmem &S,
-                                              unsigned &chunk_seq, unsigned &fp_seq, bool &ok) {
+                                              int seg_lo, int seg_hi, int g, int it, int rmode,
+                                              ScoreSmem &S, unsigned &chunk_seq,
+                                              unsigned &fp_seq, bool &ok) {
+    const bool exact = rmode == 0;
     const Segment sg{0, seg_lo, seg_hi, 0};
     const int warps = blockDim.x >> 5;
     constexpr int kTpw = (THREADS == 512) ? 2 : 1;  // tiles per consumer warp and chunk
@@ -570,6 +592,23 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
     if (threadIdx.x == 0) {
         *S.qn = 0;
         *S.acc = 0;
+        *S.xmax = 0;
+    }
+    if (rmode == 2) {
+        // switch to the ordered residual: the segment's columns that are
+        // already nonzero enter their rows' contributor records (r itself is
+        // exact and current, so no row is marked touched)
+        const long long c1 = min((long long)P.n, (long long)seg_hi * kTile);
+        for (long long j = (long long)seg_lo * kTile + threadIdx.x; j < c1; j += blockDim.x) {
+            if (__ldcg(P.x_hat + j) != 0.0) {
+                int32_t rows[DMAX];
+#pragma unroll
+                for (int t = 0; t < DMAX; ++t)
+                    rows[t] = (t < P.d) ? __ldg(P.csc_rows + (size_t)j * P.d + t) : 0;
+                P.in_slots[j] = 1;
+                enter_slots<DMAX>(P, (int)j, rows, P.d);
+            }
+        }
     }
     __syncthreads();
 
@@ -604,14 +643,14 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
         const bool wide = fp16_for(P.m);
         if (P.d == DMAX) {
             if (wide)
-                consume_segment<DMAX, THREADS, true, true>(a, P, sg, per, nchunks, chunk_seq, S, wb, ok);
+                consume_segment<DMAX, THREADS, true, true>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, ok);
             else
-                consume_segment<DMAX, THREADS, true, false>(a, P, sg, per, nchunks, chunk_seq, S, wb, ok);
+                consume_segment<DMAX, THREADS, true, false>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, ok);
         } else {
             if (wide)
-                consume_segment<DMAX, THREADS, false, true>(a, P, sg, per, nchunks, chunk_seq, S, wb, ok);
+                consume_segment<DMAX, THREADS, false, true>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, ok);
             else
-                consume_segment<DMAX, THREADS, false, false>(a, P, sg, per, nchunks, chunk_seq, S, wb, ok);
+                consume_segment<DMAX, THREADS, false, false>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, ok);
         }
     }
     chunk_seq += nchunks;
@@ -620,14 +659,75 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
     if (a.stamps && blockIdx.x == 0 && threadIdx.x == 0 && g < kMaxStampIters)
         a.stamps[kSubBase + 3 * g + 1] = globaltimer();
 
-    score_queue<DMAX>(a, P, S.queue, min(*S.qn, a.queue_cap), S.acc, ok);
+    score_queue<DMAX>(a, P, S.queue, min(*S.qn, a.queue_cap), S.acc, ok, exact, S.xmax);
     // one global atomic per CTA and segment (all warps' counts summed on chip)
     __syncthreads();
     if (threadIdx.x == 0) {
         if (*S.acc) atomicAdd(acc_slot, *S.acc);
+        if (exact && *S.xmax) atomicMax(&P.ctrl->xmax[(it + 1) & 1], *S.xmax);
         if (a.stamps && blockIdx.x == 0 && g < kMaxStampIters)
             a.stamps[kSubBase + 3 * g + 2] = globaltimer();
     }
+}
+
+// ---- exactness certificate of the incremental residual --------------------
+//
+// While every value the method forms -- y_i, r_i, x_hat_j, omega, and every
+// partial sum of a row -- is an integer multiple of 2^e (e: the lowest set
+// bit over the nonzero y_i) and below 2^(e+53) in magnitude, every binary64
+// addition and subtraction of the decode is exact.  Then the ordered row sum
+// of Alg. 2's residual equals the sum in any order, and r can be kept by
+// subtracting each accepted omega from its column's rows as it is accepted.
+// By induction all values stay on the grid of y (omega is a value of r,
+// x_hat_j a sum of omegas); the magnitudes at iteration t are bounded by
+//   |y_i| + deg * (max|x_hat| + 2 max|r|)
+// (a row's partial sums of x_hat, and r_i minus the omegas accepted in its
+// row during the iteration).  The test below asks for that bound to stay
+// under 2^(e+51), a factor 4 below the limit, which covers the rounding of
+// the bound's own evaluation.  Every CTA evaluates it from the same stored
+// maxima (written before the previous grid barrier), so all agree.
+__device__ __forceinline__ bool exact_certified(const DecodeCtrl *c, int it, int debug_flags) {
+    if ((debug_flags & kFlagOrdered) || ((debug_flags & kFlagSwitch) && it >= 2)) return false;
+    const int gb = __ldcg(&c->grid_b);
+    if (gb == 0) return true;  // y == 0: nothing is ever added
+    const int e = 1100 - gb;
+    const double Y = __longlong_as_double((long long)__ldcg(&c->ymax));
+    const double R = __longlong_as_double((long long)__ldcg(&c->rmax[it & 1]));
+    const double X = __longlong_as_double((long long)__ldcg(&c->xmax[it & 1]));
+    const double bound = Y + (double)__ldcg(&c->deg) * (X + 2.0 * R);
+    if (e + 51 > 1023) return true;
+    return bound < ldexp(1.0, e + 51);
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, v, o);
+        v = t > v ? t : v;
+    }
+    return v;
+}
+
+// Residual phase of a problem whose incremental residual is exact: r_next
+// already holds the new residual; copy the rows that changed into r, with
+// their fingerprints, and return this warp's exact change of ||r||_0 and
+// largest |r_i| (bits), both valid in every lane.
+__device__ __forceinline__ long long residual_exact_tile(const ProblemDev &P, int tile, int lane,
+                                                         unsigned long long &rmax) {
+    const int i = tile * kTile + lane;
+    long long delta = 0;
+    unsigned long long mag = 0;
+    if (i < P.m) {
+        const double v = __ldcg(P.r_next + i), o = __ldcg(P.r + i);
+        if (value_bits(v) != value_bits(o)) {
+            P.r[i] = v;
+            store_fp(P, i, v);
+        }
+        delta = (long long)(v != 0.0) - (long long)(o != 0.0);
+        mag = value_bits(v) & 0x7fffffffffffffffull;
+    }
+    rmax = warp_max_u64(mag);
+    return warp_sum_ll(delta);
 }
 
 // One row of the residual phase.  The touched flag, the row's slot record,
@@ -687,6 +787,69 @@ static __device__ __noinline__ long long residual_overflow_row(const ProblemDev 
     return delta;
 }
 
+// Init of one row: r <- y (both copies), fingerprint, empty record; and the
+// row's part of ||y||_0 and of the certificate's constants (lowest set bit
+// over the nonzero y_i, largest |y_i|, largest row degree).
+struct InitStats {
+    long long nz = 0;
+    unsigned long long ymax = 0;
+    int gridb = 0, deg = 0;
+};
+
+__device__ __forceinline__ void init_row(const ProblemDev &P, int i, InitStats &st) {
+    const double v = __ldg(P.y + i);
+    P.r[i] = v;
+    P.r_next[i] = v;
+    store_fp(P, i, v);
+    P.touched[i] = 0;
+    P.slots[(size_t)i * kSlotRec] = 0;
+    const unsigned long long b = value_bits(v) & 0x7fffffffffffffffull;
+    if (b) {
+        ++st.nz;
+        st.ymax = b > st.ymax ? b : st.ymax;
+        st.gridb = max(st.gridb, 1100 - lowbit_exponent(b));
+    }
+    st.deg = max(st.deg, (int)(__ldg(P.csr_ptr + i + 1) - __ldg(P.csr_ptr + i)));
+}
+
+__device__ __forceinline__ void init_stats_begin(long long &s_sum, unsigned long long &s_umax,
+                                                 int &s_gridb, int &s_deg) {
+    if (threadIdx.x == 0) {
+        s_sum = 0;
+        s_umax = 0;
+        s_gridb = 0;
+        s_deg = 0;
+    }
+    __syncthreads();
+}
+
+// Warp, then CTA, then one set of global atomics per CTA and problem.
+__device__ __forceinline__ void init_stats_end(const ProblemDev &P, const InitStats &st, int lane,
+                                               long long &s_sum, unsigned long long &s_umax,
+                                               int &s_gridb, int &s_deg) {
+    const long long nz = warp_sum_ll(st.nz);
+    const unsigned long long ym = warp_max_u64(st.ymax);
+    const int gb = __reduce_max_sync(0xffffffffu, (unsigned)st.gridb);
+    const int dg = __reduce_max_sync(0xffffffffu, (unsigned)st.deg);
+    if (lane == 0) {
+        if (nz) atomicAdd(reinterpret_cast<unsigned long long *>(&s_sum), (unsigned long long)nz);
+        if (ym) atomicMax(&s_umax, ym);
+        if (gb) atomicMax(&s_gridb, gb);
+        if (dg) atomicMax(&s_deg, dg);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        DecodeCtrl *c = P.ctrl;
+        if (s_sum) atomicAdd(reinterpret_cast<unsigned long long *>(&c->r0), (unsigned long long)s_sum);
+        if (s_umax) {
+            atomicMax(&c->ymax, s_umax);
+            atomicMax(&c->rmax[0], s_umax);
+        }
+        if (s_gridb) atomicMax(&c->grid_b, s_gridb);
+        if (s_deg) atomicMax(&c->deg, s_deg);
+    }
+}
+
 template <int DMAX, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ EngineArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -695,6 +858,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
     __shared__ int s_qn;
     __shared__ unsigned long long s_acc;
     __shared__ long long s_sum;
+    __shared__ unsigned long long s_xmax, s_umax;
+    __shared__ int s_gridb, s_deg;
     __shared__ int s_ovf_n;
     __shared__ int s_ovf[kOvfCap];  // rows whose sum needs the whole CSR row
     __shared__ int s_wbuf[(kWarps - 1) * kWbufPerWarp];
@@ -707,12 +872,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
     long long *s_pref = reinterpret_cast<long long *>(
         reinterpret_cast<char *>(s_status) + ((a.P + 15) / 16) * 16);  // a.P + 1 entries
     int *s_base = reinterpret_cast<int *>(s_pref + a.P + 1);          // a.P entries
+    int8_t *s_rmode = reinterpret_cast<int8_t *>(s_base + a.P);        // a.P entries
     S.full = s_bars;
     S.empty = s_bars + kMaxStages;
     S.fp_bar = &s_bars[2 * kMaxStages];
     S.qn = &s_qn;
     S.acc = &s_acc;
     S.wbuf = s_wbuf;
+    S.xmax = &s_xmax;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned bar = 0, chunk_seq = 0, fp_seq = 0;
     bool ok = true;
@@ -730,6 +897,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
     if (a.resume && blockIdx.x == 0)
         for (int p = threadIdx.x; p < a.P; p += THREADS)
             for (int q = 0; q < 4; ++q) problem(a, p).ctrl->acc[q] = 0;
+    // residual mode carried over from an earlier launch (0 for a fresh
+    // problem); CTA 0 writes the flag only after the init barrier
+    for (int p = threadIdx.x; p < a.P; p += THREADS)
+        s_rmode[p] = (int8_t)(__ldcg(&problem(a, p).ctrl->ordered) ? 1 : 0);
     __syncthreads();
 
     // ---- init: x_hat <- 0, r <- y (Alg. 2, first line) --------------------
@@ -742,23 +913,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
             P.x_hat[j] = 0.0;
             P.in_slots[j] = 0;
         }
-        if (threadIdx.x == 0) s_sum = 0;
-        __syncthreads();
-        long long nz = 0;
-        for (long long i = gtid; i < P.m; i += gstride) {
-            const double v = __ldg(P.y + i);
-            P.r[i] = v;
-            store_fp(P, i, v);
-            P.touched[i] = 0;
-            P.slots[(size_t)i * kSlotRec] = 0;
-            nz += (v != 0.0);
-        }
-        nz = warp_sum_ll(nz);
-        if (lane == 0 && nz)
-            atomicAdd(reinterpret_cast<unsigned long long *>(&s_sum), (unsigned long long)nz);
-        __syncthreads();
-        if (threadIdx.x == 0 && s_sum)
-            atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0), (unsigned long long)s_sum);
+        init_stats_begin(s_sum, s_umax, s_gridb, s_deg);
+        InitStats st;
+        for (long long i = gtid; i < P.m; i += gstride) init_row(P, (int)i, st);
+        init_stats_end(P, st, lane, s_sum, s_umax, s_gridb, s_deg);
     } else {
         build_partition<THREADS>(a, s_status, s_pref, kPartInitCols);
         for_my_segments(a, s_status, s_pref, kPartInitCols,
@@ -774,28 +932,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
         build_partition<THREADS>(a, s_status, s_pref, kPartInitRows);
         for_my_segments(a, s_status, s_pref, kPartInitRows,
                         [&](int, const ProblemDev &P, int t0, int t1) {
-                            if (threadIdx.x == 0) s_sum = 0;
-                            __syncthreads();
+                            init_stats_begin(s_sum, s_umax, s_gridb, s_deg);
+                            InitStats st;
                             for (int t = t0 + warp; t < t1; t += kWarps) {
                                 const int i = t * kTile + lane;
-                                long long nz = 0;
-                                if (i < P.m) {
-                                    const double v = __ldg(P.y + i);
-                                    P.r[i] = v;
-                                    store_fp(P, i, v);
-                                    P.touched[i] = 0;
-                                    P.slots[(size_t)i * kSlotRec] = 0;
-                                    nz = (v != 0.0);
-                                }
-                                nz = warp_sum_ll(nz);
-                                if (lane == 0 && nz)
-                                    atomicAdd(reinterpret_cast<unsigned long long *>(&s_sum),
-                                              (unsigned long long)nz);
+                                if (i < P.m) init_row(P, i, st);
                             }
-                            __syncthreads();
-                            if (threadIdx.x == 0 && s_sum)
-                                atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0),
-                                          (unsigned long long)s_sum);
+                            init_stats_end(P, st, lane, s_sum, s_umax, s_gridb, s_deg);
                         });
     }
     if (!grid_barrier(a, bar++)) {
@@ -829,19 +972,39 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
         if (!__syncthreads_or(any)) break;
         if (blockIdx.x == 0)
             for (int p = threadIdx.x; p < a.P; p += THREADS) problem(a, p).ctrl->acc[(g + 2) & 3] = 0;
+        // residual mode of this iteration, per problem (the same decision in
+        // every CTA: it reads maxima stored before the last grid barrier)
+        for (int p = threadIdx.x; p < a.P; p += THREADS) {
+            if (s_status[p] != kRunning || s_rmode[p] == 1) continue;
+            const ProblemDev &P = problem(a, p);
+            const int it = s_base[p] + g;
+            if (s_rmode[p] == 2) {
+                s_rmode[p] = 1;
+            } else if (!exact_certified(P.ctrl, it, a.debug_flags)) {
+                s_rmode[p] = 2;
+                if (blockIdx.x == 0) P.ctrl->ordered = 1;
+            } else if (blockIdx.x == 0) {
+                P.ctrl->rmax[(it + 1) & 1] = 0;
+                atomicMax(&P.ctrl->xmax[(it + 1) & 1], __ldcg(&P.ctrl->xmax[it & 1]));
+            }
+        }
+        __syncthreads();
 
         // ---- score + apply ------------------------------------------------
         if (!a.probs) {
             const long long tiles = (a.single.n + kTile - 1) / kTile;
             const int t0 = (int)(tiles * blockIdx.x / gridDim.x);
             const int t1 = (int)(tiles * (blockIdx.x + 1) / gridDim.x);
-            if (t1 > t0) score_segment<DMAX, THREADS>(a, a.single, t0, t1, g, S, chunk_seq, fp_seq, ok);
+            if (t1 > t0)
+                score_segment<DMAX, THREADS>(a, a.single, t0, t1, g, s_base[0] + g, s_rmode[0], S,
+                                             chunk_seq, fp_seq, ok);
         } else {
             build_partition<THREADS>(a, s_status, s_pref, kPartScore);
             for_my_segments(a, s_status, s_pref, kPartScore,
-                            [&](int, const ProblemDev &P, int t0, int t1) {
+                            [&](int p, const ProblemDev &P, int t0, int t1) {
                                 if (!__syncthreads_and(ok)) return;
-                                score_segment<DMAX, THREADS>(a, P, t0, t1, g, S, chunk_seq, fp_seq, ok);
+                                score_segment<DMAX, THREADS>(a, P, t0, t1, g, s_base[p] + g,
+                                                             s_rmode[p], S, chunk_seq, fp_seq, ok);
                             });
         }
         if (!__syncthreads_and(ok)) {
@@ -861,7 +1024,33 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
         }
 
         // ---- residual + ||r||_0 ---------------------------------------------
-        auto residual_segment = [&](const ProblemDev &P, int t0, int t1) {
+        auto residual_segment = [&](int p, const ProblemDev &P, int t0, int t1) {
+            if (s_rmode[p] == 0) {
+                // exact incremental residual: a streaming pass over the rows
+                if (threadIdx.x == 0) {
+                    s_sum = 0;
+                    s_umax = 0;
+                }
+                __syncthreads();
+                for (int t = t0 + warp; t < t1; t += kWarps) {
+                    unsigned long long rmax;
+                    const long long delta = residual_exact_tile(P, t, lane, rmax);
+                    if (lane == 0) {
+                        if (delta)
+                            atomicAdd(reinterpret_cast<unsigned long long *>(&s_sum),
+                                      (unsigned long long)delta);
+                        if (rmax) atomicMax(&s_umax, rmax);
+                    }
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    if (s_sum)
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->r0),
+                                  (unsigned long long)s_sum);
+                    if (s_umax) atomicMax(&P.ctrl->rmax[(s_base[p] + g + 1) & 1], s_umax);
+                }
+                return;
+            }
             if (threadIdx.x == 0) {
                 s_sum = 0;
                 s_ovf_n = 0;
@@ -885,12 +1074,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
         };
         if (!a.probs) {
             const long long tiles = (a.single.m + kTile - 1) / kTile;
-            residual_segment(a.single, (int)(tiles * blockIdx.x / gridDim.x),
+            residual_segment(0, a.single, (int)(tiles * blockIdx.x / gridDim.x),
                              (int)(tiles * (blockIdx.x + 1) / gridDim.x));
         } else {
             build_partition<THREADS>(a, s_status, s_pref, kPartRows);
             for_my_segments(a, s_status, s_pref, kPartRows,
-                            [&](int, const ProblemDev &P, int t0, int t1) { residual_segment(P, t0, t1); });
+                            [&](int p, const ProblemDev &P, int t0, int t1) {
+                                residual_segment(p, P, t0, t1);
+                            });
         }
         if (!grid_barrier(a, bar++)) {
             fail_out(a);

@@ -34,9 +34,19 @@ struct alignas(64) DecodeCtrl {
     int status;                 // kRunning or CCS_CONVERGED / _STALLED / _MAX_ITER
     int error;                  // ErrorBits
     int max_iter;
-    long long pad;
+    // Exactness certificate of the incremental residual (persistent engine):
+    int grid_b;                 // 1100 - (exponent of the lowest set bit over the
+                                // nonzero y_i); 0 when y == 0
+    int deg;                    // largest row degree of A
+    unsigned long long ymax;    // bits of max |y_i|
+    unsigned long long rmax[2]; // bits of max |r_i| at the start of iteration t
+                                // (slot t & 1)
+    unsigned long long xmax[2]; // bits of an upper bound of every |x_hat_j| so far
+                                // at the start of iteration t (slot t & 1)
+    int ordered;                // 1 once the problem runs the ordered residual
+    int pad[5];
 };
-static_assert(sizeof(DecodeCtrl) == 64, "DecodeCtrl layout");
+static_assert(sizeof(DecodeCtrl) == 128, "DecodeCtrl layout");
 
 // Device view of one problem plus its slice of the workspace.
 struct ProblemDev {
@@ -51,6 +61,8 @@ struct ProblemDev {
     const double *y;
     double *x_hat;
     double *r;
+    double *r_next;       // m: r updated in place by the accepted pairs while the
+                          // incremental residual is exact (persistent engine)
     int64_t *r0_hist;     // may be null
     DecodeCtrl *ctrl;
     uint8_t *touched;     // m: rows whose sum must be recomputed
@@ -87,7 +99,9 @@ __host__ inline size_t decode_ws_layout(int n, int m, ProblemDev *pd, char *base
     char *in_slots = take((size_t)n);
     char *slots = take((size_t)m * kSlotRec * 4);
     char *fp = take(fp_bytes(m));
+    char *r_next = take((size_t)m * 8);
     if (pd) {
+        pd->r_next = reinterpret_cast<double *>(r_next);
         pd->fp = reinterpret_cast<uint8_t *>(fp);
         pd->touched = reinterpret_cast<uint8_t *>(touched);
         pd->in_slots = reinterpret_cast<uint8_t *>(in_slots);

@@ -307,6 +307,38 @@ def test_engines_match_oracle(ccs, orc, engine, shape):
     assert_same_decode(g, ref)
 
 
+RESIDUAL_CASES = [("small", lambda: inputs.plain_small(seed=3)),
+                  ("small-raw", lambda: inputs.plain_small(seed=3, model="gauss-raw")),
+                  ("small-pm1", lambda: inputs.plain_small(seed=3, model="pm1")),
+                  ("extreme-scaled", lambda: inputs.extreme_undersampling(0.25, d=9, seed=13,
+                                                                          log2n=20)),
+                  ("mid", lambda: inputs.make_problem(200000, 20000, 7, 4000, 17))]
+
+
+@pytest.mark.parametrize("flags", [0, 2, 4])
+@pytest.mark.parametrize("case", [c[0] for c in RESIDUAL_CASES])
+def test_residual_modes_match_oracle(ccs, orc, case, flags):
+    """The persistent engine keeps r by exact atomic updates while its
+    certificate holds, else by ordered row sums; debug bit 1 forces the
+    ordered form from the start, bit 2 a switch at iteration 2 (its records
+    rebuilt on the way).  Every form equals the oracle bit for bit."""
+    p = dict(RESIDUAL_CASES)[case]()
+    g, ref = _decode_both(ccs, orc, p, engine=ccs.ENGINE_PERSISTENT, debug_flags=flags,
+                          max_iter=40)
+    assert_same_decode(g, ref)
+
+
+def test_residual_mode_switch_in_batch(ccs, orc):
+    """A batch where the certificate fails at iteration 2 for every problem:
+    each result still equals the oracle."""
+    probs = inputs.batch_problems(12, seed=31, log2n_hi=15.0)
+    items = [device_problem(ccs, p) for p in probs]
+    outs = ccs.decode_batch(items, history=True, debug_flags=4)
+    for p, g in zip(probs, outs):
+        A, y_ref = oracle_problem(orc, p)
+        assert_same_decode(g, orc.parallel_l0(A, p.m, y_ref))
+
+
 def test_watchdog_times_out_and_context_survives(ccs, orc):
     """Test hook: CTA 0 never arrives at the first score barrier, so every
     CTA's bounded wait runs out (200 ms); the call reports CCS_ETIMEOUT and
