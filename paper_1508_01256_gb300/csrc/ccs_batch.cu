@@ -88,20 +88,27 @@ static int decode_batch_impl(const ccs_problem *probs, int32_t count, const ccs_
         }
         return CCS_OK;
     }
-    // Problems with d <= 8 and d > 8 run on different kernel instances (the
-    // register-resident arrays are sized by the largest d of a launch), so a
-    // mixed batch goes out as two launches, one per class, each over the
-    // whole GPU.  Every problem's result is the same either way.
+    // A batch goes out as up to four launches, one per class, each over the
+    // whole GPU: d <= 8 and d > 8 run on different kernel instances (the
+    // register-resident arrays are sized by the largest d of a launch), and
+    // problems whose fingerprints do not fit shared memory would shrink every
+    // other problem's launch plan (fewer stages, a smaller queue) and its
+    // thread count.  Every problem's result is the same either way.
+    std::vector<int> cls(count);
+    for (int32_t q = 0; q < count; ++q)
+        cls[q] = (pds[q].d > 8 ? 2 : 0) + (engine_fp_fits(pds[q], p) ? 0 : 1);
     std::vector<int> order;
-    int sizes[2] = {0, 0};
-    for (int cls = 0; cls < 2; ++cls)
+    int sizes[4] = {0, 0, 0, 0};
+    int groups = 0;
+    for (int c = 0; c < 4; ++c) {
+        int cnt = 0;
         for (int32_t q = 0; q < count; ++q)
-            if ((pds[q].d > 8) == (cls == 1)) {
+            if (cls[q] == c) {
                 order.push_back(q);
-                ++sizes[cls];
+                ++cnt;
             }
-    const int groups = (sizes[0] && sizes[1]) ? 2 : 1;
-    if (groups == 1) sizes[0] = count;
+        if (cnt) sizes[groups++] = cnt;
+    }
     // descriptors in launch order; each launch's control blocks sit at the
     // front of the header, and out_slot keeps the caller's index
     std::vector<ProblemDev> sub(count);

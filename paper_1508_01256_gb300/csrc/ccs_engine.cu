@@ -252,6 +252,24 @@ static void fill_args(EngineArgs &a, const LaunchPlan &L, int P, const ccs_param
 }
 
 
+bool engine_fp_fits(const ProblemDev &pd, const ccs_params &prm) {
+    // the fingerprint part of plan_launch for one problem, without the
+    // occupancy query (called once per problem of a batch)
+    const int sched = schedule_for(pd.d, prm.schedule);
+    engine_fn fn = engine_kernel(pd.d, sched);
+    int dev = 0;
+    if (!fn || cudaGetDevice(&dev) != cudaSuccess) return false;
+    const size_t smem_limit = max_dynamic_smem(dev, fn);
+    const int threads = sched == 1 ? 1024 : (sched == 3 ? 768 : 512);
+    const int tpw = sched == 2 ? 2 : 1;
+    const size_t stage_bytes = align_up((size_t)(threads / 32 - 1) * tpw * kTile * pd.d * 4, 128);
+    const size_t status_bytes = 16 + sizeof(long long) * 2 + sizeof(int) + 1;
+    const size_t fixed = status_bytes + 256 + kMinQueue * (size_t)(pd.d + 1) * 4;
+    if (smem_limit < fixed + 2 * stage_bytes) return false;
+    const size_t need = align_up((size_t)pd.m * (fp16_for(pd.m) ? 2 : 1), 16);
+    return need <= smem_limit - fixed - 2 * stage_bytes;
+}
+
 int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, char *ws,
                cudaStream_t s, ccs_result *dev_out) {
     LaunchPlan L;

@@ -292,13 +292,23 @@ __device__ __forceinline__ void for_my_segments(const EngineArgs &a, const int8_
         if (pref[mid + 1] > B0) hi = mid;
         else lo = mid + 1;
     }
+    // the segment's descriptor is staged in shared memory: the segment's
+    // code reads its fields many times, and a.probs lives in global memory
+    __shared__ ProblemDev s_seg;
     for (int p = lo; p < a.P && pref[p] < B1; ++p) {
-        const ProblemDev &P = problem(a, p);
-        if (!part_on(a, P, status[p], kind)) continue;
-        const long long w = part_weight(P, kind), tiles = part_tiles(P, kind);
+        const ProblemDev &G = problem(a, p);
+        if (!part_on(a, G, status[p], kind)) continue;
+        const long long w = part_weight(G, kind), tiles = part_tiles(G, kind);
         const long long t0 = B0 > pref[p] ? (B0 - pref[p] + w - 1) / w : 0;
         const long long t1 = min(tiles, (B1 - pref[p] + w - 1) / w);
-        if (t1 > t0) fn(p, P, (int)t0, (int)t1);
+        if (t1 > t0) {
+            __syncthreads();  // the previous segment is done with s_seg
+            if (threadIdx.x < (int)(sizeof(ProblemDev) / sizeof(int)))
+                reinterpret_cast<int *>(&s_seg)[threadIdx.x] =
+                    reinterpret_cast<const int *>(&G)[threadIdx.x];
+            __syncthreads();
+            fn(p, s_seg, (int)t0, (int)t1);
+        }
     }
 }
 

@@ -172,6 +172,9 @@ int decode_host_loop(const ProblemDev &P, const ccs_params &p, ccs_result *out, 
 // persistent engine (ccs_engine.cu).  The workspace starts with
 // engine_header_bytes(P) bytes: EngineSync, P DecodeCtrl, engine scratch.
 size_t engine_header_bytes(int P);
+// Whether the problem, launched alone with these params, keeps its
+// fingerprints in shared memory (false also when no launch shape fits).
+bool engine_fp_fits(const ProblemDev &pd, const ccs_params &prm);
 DecodeCtrl *header_ctrl(char *ws, int p);
 int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, char *ws,
                cudaStream_t s, ccs_result *dev_out = nullptr);
