@@ -330,6 +330,10 @@ def batched_vs_plain(ccs, dev, count: int, seed: int, reps: int = 3):
     prm = ccs.params()
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    # launch shapes of the batched launches picked by the library's
+    # autotuner (untimed); the plain single-problem launches keep the rule
+    tuned = ccs.ccs_autotune(pbs, prm, ws_b, stream)
+    torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     tb, tp = [], []
     for rep in range(reps + 1):
@@ -363,6 +367,7 @@ def batched_vs_plain(ccs, dev, count: int, seed: int, reps: int = 3):
             tg.append(ev[0].elapsed_time(ev[1]))
     rg = graph.read_results()
     graph.close()
+    ccs.ccs_autotune_reset()
     rb = ccs.results_from_device(res_b, count)
     rp = ccs.results_from_device(res_p, count)
     same = all(a.status == b.status == c.status and a.iterations == b.iterations == c.iterations
@@ -382,10 +387,12 @@ def batched_vs_plain(ccs, dev, count: int, seed: int, reps: int = 3):
             "plain_decodes_per_s": count / (mp / 1000.0), "batched_ms": mb, "plain_ms": mp,
             "graph_batched_decodes_per_s": count / (mg / 1000.0), "graph_ms": mg,
             "speedup": mp / mb, "batched_column_updates_per_s": cols_total / (mb / 1000.0),
+            "autotuned_shapes": [t for t in tuned if t],
             "same_results": same, "converged": conv, "exact_recovery": exact,
             "max_iterations": max(a.iterations for a in rb),
             "workload": "n log-uniform 2^12..2^20, m/n in {0.01,0.05,0.1,0.3}, "
-                        "k/m in {0.05,0.1,0.2}, d in {5,7,9,11}, gauss-grid"}
+                        "k/m in {0.05,0.1,0.2}, d in {5,7,9,11}, gauss-grid; launch shapes "
+                        "autotuned (1: 1024 threads, 2: 512, 3: 768 a CTA)"}
 
 
 def serving_run(ccs, dev, count: int, seed: int, load: float = 0.7,

@@ -254,6 +254,26 @@ CCS_API int ccs_decode_batch_async(const ccs_problem *probs, int32_t count,
                                    const ccs_params *p, ccs_result *out_dev,
                                    void *ws, size_t ws_bytes, ccs_stream_t stream);
 
+/* ---- launch-shape autotuner ---------------------------------------------------
+ *
+ * Not in the paper (its method fixes no launch configuration).  A batched
+ * decode goes out as up to four launches, one per class of problem (d <= 8
+ * or d > 8; fingerprints of r in shared memory or not).  ccs_autotune
+ * decodes `probs` as ccs_decode_batch would, but runs each launch group with
+ * every launch shape its kernel instances offer (CTAs of 1024, 768 or 512
+ * threads for d <= 8; 512 for d > 8), twice each, timing the second run
+ * with CUDA events on `stream`.  The fastest shape of each group is recorded
+ * in a table inside the library, per device and class (largest d of the
+ * launch, fingerprint fit); from then on every launch on that device with
+ * p->schedule == 0 in that class uses it.  tuned[0..3] receives the shape
+ * picked for each group in launch order (0 for groups that do not exist).
+ * Arguments, workspace and errors as ccs_decode_batch; the outputs hold the
+ * last run's decode (every shape gives the same results).  Blocks the
+ * calling thread.  ccs_autotune_reset clears the table.                   */
+CCS_API int ccs_autotune(const ccs_problem *probs, int32_t count, const ccs_params *p,
+                         void *ws, size_t ws_bytes, ccs_stream_t stream, int32_t *tuned);
+CCS_API void ccs_autotune_reset(void);
+
 /* ---- CUDA graph of a batched decode -----------------------------------------
  *
  * ccs_batch_graph_create captures one ccs_decode_batch_async launch of these

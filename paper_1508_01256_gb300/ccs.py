@@ -125,6 +125,11 @@ def lib() -> ctypes.CDLL:
                                                    ctypes.POINTER(Params), P, P, sz, P]
         l.ccs_decode_batch_async.argtypes = [ctypes.POINTER(Problem), i32, ctypes.POINTER(Params),
                                              P, P, sz, P]
+        l.ccs_autotune.argtypes = [ctypes.POINTER(Problem), i32, ctypes.POINTER(Params), P, sz, P,
+                                   ctypes.POINTER(i32)]
+        l.ccs_autotune.restype = ctypes.c_int
+        l.ccs_autotune_reset.argtypes = []
+        l.ccs_autotune_reset.restype = None
         l.ccs_decode_parallel_l0_noalloc.argtypes = [i32, i32, i32, P, P, P, P, P, P, P,
                                                      ctypes.POINTER(Params),
                                                      ctypes.POINTER(Result), P]
@@ -253,6 +258,22 @@ def ccs_decode_batch_async(probs, p: Params | None, out_dev, ws, stream=None):
                                       _ptr(out_dev), _ptr(ws), ws.numel() * ws.element_size(),
                                       _stream(stream))
     _check(rc, "ccs_decode_batch_async")
+
+
+def ccs_autotune(probs, p: Params | None, ws, stream=None) -> list:
+    """Time every launch shape per launch group of this batch and record the
+    fastest in the library's table; returns the shape picked per group."""
+    cnt = len(probs)
+    arr = (Problem * cnt)(*probs)
+    tuned = (ctypes.c_int32 * 4)()
+    rc = lib().ccs_autotune(arr, cnt, ctypes.byref(p) if p is not None else None, _ptr(ws),
+                            ws.numel() * ws.element_size(), _stream(stream), tuned)
+    _check(rc, "ccs_autotune")
+    return [int(t) for t in tuned]
+
+
+def ccs_autotune_reset() -> None:
+    lib().ccs_autotune_reset()
 
 
 RESULT_BYTES = ctypes.sizeof(Result)

@@ -1,4 +1,5 @@
 // ccs_batch.cu -- many independent decodes in one persistent launch.
+#include <algorithm>
 #include <vector>
 
 #include "ccs_internal.cuh"
@@ -14,9 +15,66 @@ static size_t batch_ws(const ccs_problem *probs, int32_t count) {
     return engine_header_bytes(count) + total;
 }
 
+// Time every launch shape the kernel instances offer for each launch group
+// (d <= 8: 1024, 768 and 512 threads; d > 8: 512 only) and record the
+// fastest for the group's class.  Each candidate decodes the group twice;
+// the second run is timed.  tuned[g] receives group g's choice (0..3 more
+// entries are set to 0).
+static int autotune_groups(std::vector<ProblemDev> &sub, const int *sizes, int groups,
+                           const ccs_params &p, char *hdr, cudaStream_t s, int32_t *tuned) {
+    int dev = 0;
+    CCS_CUDA_TRY(cudaGetDevice(&dev));
+    cudaEvent_t e0, e1;
+    CCS_CUDA_TRY(cudaEventCreate(&e0));
+    CCS_CUDA_TRY(cudaEventCreate(&e1));
+    std::vector<ccs_result> part(sub.size());
+    int rc = CCS_OK;
+    for (int g = 0; g < 4; ++g) tuned[g] = 0;
+    for (int g = 0, first = 0; g < groups && rc == CCS_OK; first += sizes[g], ++g) {
+        int dmax = 1;
+        bool fits = true;
+        for (int u = 0; u < sizes[g]; ++u) {
+            dmax = std::max(dmax, sub[first + u].d);
+            fits = fits && engine_fp_fits(sub[first + u], p);
+        }
+        const int cands_small[3] = {1, 3, 2}, cands_large[1] = {2};
+        const int *cands = dmax <= 8 ? cands_small : cands_large;
+        const int ncand = dmax <= 8 ? 3 : 1;
+        int best = 0;
+        float best_ms = 0.0f;
+        for (int c = 0; c < ncand && rc == CCS_OK; ++c) {
+            ccs_params q = p;
+            q.schedule = cands[c];
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2 && rc == CCS_OK; ++rep) {
+                if (cudaEventRecord(e0, s) != cudaSuccess) rc = CCS_ECUDA;
+                if (rc == CCS_OK)
+                    rc = engine_run(sub.data() + first, sizes[g], q, part.data() + first, hdr, s);
+                if (rc == CCS_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
+                                     cudaEventSynchronize(e1) != cudaSuccess ||
+                                     cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                    rc = CCS_ECUDA;
+            }
+            if (rc == CCS_OK && (best == 0 || ms < best_ms)) {
+                best = cands[c];
+                best_ms = ms;
+            }
+        }
+        if (rc == CCS_OK) {
+            tuned_schedule_set(dev, dmax, fits, best);
+            tuned[g] = best;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == CCS_ECUDA) set_last_error("ccs_autotune: a CUDA event call failed");
+    return rc;
+}
+
 }  // namespace ccs
 
 using namespace ccs;
+
 
 extern "C" size_t ccs_batch_workspace_size(const ccs_problem *probs, int32_t count) {
     if (!probs || count < 1) return 0;
@@ -25,7 +83,8 @@ extern "C" size_t ccs_batch_workspace_size(const ccs_problem *probs, int32_t cou
 
 static int decode_batch_impl(const ccs_problem *probs, int32_t count, const ccs_params *params,
                              ccs_result *out, void *ws, size_t ws_bytes, ccs_stream_t stream,
-                             ccs_result *dev_out, cudaGraphExec_t *capture = nullptr) {
+                             ccs_result *dev_out, cudaGraphExec_t *capture = nullptr,
+                             int32_t *tuned = nullptr) {
     if (!probs || count < 1 || !out || !ws) {
         set_last_error("ccs_decode_batch: bad arguments");
         return CCS_EINVAL;
@@ -119,6 +178,7 @@ static int decode_batch_impl(const ccs_problem *probs, int32_t count, const ccs_
         }
     if (capture) return engine_capture(sub.data(), sizes, groups, p, hdr, dev_out, capture);
     std::vector<ccs_result> part(count);
+    if (tuned) return autotune_groups(sub, sizes, groups, p, hdr, s, tuned);
     for (int g = 0, first = 0; g < groups; first += sizes[g], ++g) {
         rc = engine_run(sub.data() + first, sizes[g], p, part.data() + first, hdr, s, dev_out);
         if (rc != CCS_OK) return rc;
@@ -180,4 +240,19 @@ extern "C" int ccs_graph_destroy(ccs_graph *g) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     delete g;
     return CCS_OK;
+}
+
+extern "C" int ccs_autotune(const ccs_problem *probs, int32_t count, const ccs_params *params,
+                            void *ws, size_t ws_bytes, ccs_stream_t stream, int32_t *tuned) {
+    if (!tuned) {
+        set_last_error("ccs_autotune: null output");
+        return CCS_EINVAL;
+    }
+    if (params && params->engine == CCS_ENGINE_HOST_LOOP) {
+        set_last_error("ccs_autotune: tunes the persistent engine only");
+        return CCS_EINVAL;
+    }
+    std::vector<ccs_result> unused(count > 0 ? count : 1);
+    return decode_batch_impl(probs, count, params, unused.data(), ws, ws_bytes, stream, nullptr,
+                             nullptr, tuned);
 }

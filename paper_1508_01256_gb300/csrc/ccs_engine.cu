@@ -26,6 +26,28 @@ static int schedule_for(int dmax, int requested) {
     return 1;  // measured fastest for d <= 8
 }
 
+// Launch shapes picked by ccs_autotune, by device, largest d of a launch and
+// whether all its problems keep fingerprints in shared memory (0: none).
+static std::mutex g_tune_mu;
+static int g_tuned[64][kMaxD + 1][2];
+
+void tuned_schedule_set(int dev, int dmax, bool fits, int schedule) {
+    if (dev < 0 || dev >= 64 || dmax < 1 || dmax > kMaxD) return;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[dev][dmax][fits ? 1 : 0] = schedule;
+}
+
+static int tuned_schedule_get(int dev, int dmax, bool fits) {
+    if (dev < 0 || dev >= 64 || dmax < 1 || dmax > kMaxD) return 0;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tuned[dev][dmax][fits ? 1 : 0];
+}
+
+void tuned_schedule_reset() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    std::memset(g_tuned, 0, sizeof(g_tuned));
+}
+
 static engine_fn engine_kernel(int dmax, int schedule) {
     const int threads = schedule == 1 ? 1024 : (schedule == 3 ? 768 : 512);
     if (dmax < 1 || dmax > (threads == 512 ? 16 : 8)) return nullptr;
@@ -162,7 +184,17 @@ static int plan_launch(ProblemDev *pds, int P, const ccs_params &prm, LaunchPlan
         set_last_error("csc_rows must be 16-byte aligned for the persistent engine");
         return CCS_EINVAL;
     }
-    int sched = schedule_for(dmax, prm.schedule);
+    int requested = prm.schedule;
+    if (requested == 0) {
+        // a shape picked by ccs_autotune for this class of launch, if any
+        int dev = 0;
+        CCS_CUDA_TRY(cudaGetDevice(&dev));
+        bool fits_all = true;
+        for (int p = 0; p < P && fits_all; ++p) fits_all = engine_fp_fits(pds[p], prm);
+        const int t = tuned_schedule_get(dev, dmax, fits_all);
+        if (t) requested = t;
+    }
+    int sched = schedule_for(dmax, requested);
     for (int attempt = 0; attempt < 2; ++attempt) {
     engine_fn fn = engine_kernel(dmax, sched);
     const int threads = sched == 1 ? 1024 : (sched == 3 ? 768 : 512);
@@ -470,3 +502,5 @@ int engine_resume(ProblemDev *pds, int P, const ccs_params &prm, int iter_budget
 }
 
 }  // namespace ccs
+
+extern "C" CCS_API void ccs_autotune_reset(void) { ccs::tuned_schedule_reset(); }

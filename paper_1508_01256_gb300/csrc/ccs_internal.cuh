@@ -175,6 +175,11 @@ size_t engine_header_bytes(int P);
 // Whether the problem, launched alone with these params, keeps its
 // fingerprints in shared memory (false also when no launch shape fits).
 bool engine_fp_fits(const ProblemDev &pd, const ccs_params &prm);
+// Record the launch shape ccs_autotune picked for launches on device `dev`
+// whose largest d is dmax and whose problems all keep (fits) or do not all
+// keep shared-memory fingerprints.
+void tuned_schedule_set(int dev, int dmax, bool fits, int schedule);
+void tuned_schedule_reset();
 DecodeCtrl *header_ctrl(char *ws, int p);
 int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, char *ws,
                cudaStream_t s, ccs_result *dev_out = nullptr);

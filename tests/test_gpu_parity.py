@@ -476,3 +476,30 @@ def test_batch_graph_replays(ccs, orc):
         assert res.status == oref["status"] and res.iterations == oref["iterations"]
         assert np.array_equal(x_hat.cpu().numpy(), oref["x_hat"])
     g.close()
+
+
+def test_autotune_records_a_shape_and_keeps_results(ccs, orc):
+    """ccs_autotune times every launch shape of each launch group and records
+    the fastest; decodes that follow (schedule 0) use it and still equal the
+    oracle bit for bit."""
+    import torch
+    probs = inputs.batch_problems(12, seed=57, log2n_hi=15.0)
+    assert {p.d > 8 for p in probs} == {True, False}
+    items = [device_problem(ccs, p) for p in probs]
+    pbs = []
+    for (csc, ptr, cols, y), p in zip(items, probs):
+        x_hat = torch.empty(p.n, dtype=torch.float64, device="cuda")
+        r = torch.empty(p.m, dtype=torch.float64, device="cuda")
+        pbs.append(ccs.problem(csc, ptr, cols, y, x_hat, r))
+    ws = ccs.workspace(ccs.ccs_batch_workspace_size(pbs))
+    try:
+        tuned = ccs.ccs_autotune(pbs, ccs.params(), ws)
+        torch.cuda.synchronize()
+        groups = [t for t in tuned if t]
+        assert len(groups) >= 2 and all(t in (1, 2, 3) for t in groups)
+        outs = ccs.decode_batch(items, history=True)
+        for p, g in zip(probs, outs):
+            A, y_ref = oracle_problem(orc, p)
+            assert_same_decode(g, orc.parallel_l0(A, p.m, y_ref))
+    finally:
+        ccs.ccs_autotune_reset()
