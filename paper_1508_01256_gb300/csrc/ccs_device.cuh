@@ -154,6 +154,26 @@ __device__ __forceinline__ bool exact_score_values(const unsigned long long (&v)
     return best_cnt > 0 && score >= alpha;
 }
 
+// The fingerprint bound computed from gathered values v (value_bits form):
+// false when no value of the column can reach alpha (exact rejection: equal
+// values have equal fingerprints).  Cheaper than the O(d^2) compare of
+// 64-bit values that it spares most columns.
+template <int DMAX>
+__device__ __forceinline__ bool values_may_accept(const unsigned long long (&v)[DMAX], int d,
+                                                  int alpha, int mode) {
+    unsigned w[4] = {0u, 0u, 0u, 0u};
+    int c0 = 0;
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t) {
+        const unsigned f = (t < d) ? (unsigned)fingerprint_of_bits(v[t]) : 0u;
+        c0 += (t < d) & (v[t] == 0ull);
+        w[t >> 2] |= f << (8 * (t & 3));
+    }
+    const int need = (mode == CCS_SCORE_COUNT) ? alpha : alpha + c0;
+    if (d - c0 < need) return false;
+    return fingerprint_max_count<DMAX>(w[0], w[1], w[2], w[3], d) >= need;
+}
+
 // Exact score of one column from its d row indices `rows` (stride 1).
 // Returns true when the pair (j, omega) is accepted; omega's bits in *omega.
 // Equality is equality of binary64 values (bit patterns with -0.0 folded);
@@ -170,19 +190,8 @@ __device__ __forceinline__ bool exact_score(const int32_t *rows, int d, const do
     unsigned long long v[DMAX];
 #pragma unroll
     for (int t = 0; t < DMAX; ++t) v[t] = (t < d) ? value_bits(__ldcg(r + rows[t])) : 0ull;
-    if (!kPrefilter) return exact_score_values<DMAX>(v, d, alpha, mode, omega);
-    unsigned w[4] = {0u, 0u, 0u, 0u};
-    int c0 = 0;
-#pragma unroll
-    for (int t = 0; t < DMAX; ++t) {
-        const unsigned f = (t < d) ? (unsigned)fingerprint_of_bits(v[t]) : 0u;
-        c0 += (t < d) & (v[t] == 0ull);
-        w[t >> 2] |= f << (8 * (t & 3));
-    }
-    const int need = (mode == CCS_SCORE_COUNT) ? alpha : alpha + c0;
     *omega = 0ull;
-    if (d - c0 < need) return false;
-    if (fingerprint_max_count<DMAX>(w[0], w[1], w[2], w[3], d) < need) return false;
+    if (kPrefilter && !values_may_accept<DMAX>(v, d, alpha, mode)) return false;
     return exact_score_values<DMAX>(v, d, alpha, mode, omega);
 }
 

@@ -348,21 +348,37 @@ __device__ __forceinline__ void issue_chunk(const EngineArgs &a, const ProblemDe
     if (tma) bulk_g2s(S.stage + (size_t)slot * a.stage_bytes, P.csc_rows + col0 * P.d, tma, bar);
 }
 
-// Exact score and apply of one column inside the stream (problems without
-// shared-memory fingerprints, or a full queue); the rows are read again from
-// global memory, so the stream loop keeps no copy of them.
-template <int DMAX, bool kPrefilter>
+// Exact score and apply of one column inside the stream, from its rows in
+// registers.  kCandidate: the column passed the fingerprint test (the queue
+// was full), so it is likely accepted: x_hat_j and the in-slots flag are
+// loaded in the same round as the r gathers.  Otherwise (problems without
+// shared-memory fingerprints) most columns are rejected: kPrefilter applies
+// the fingerprint bound of the gathered values before the O(d^2) compare,
+// and x_hat_j is loaded only for accepted columns.
+template <int DMAX, bool kPrefilter, bool kCandidate>
 __device__ __forceinline__ bool score_inline(const EngineArgs &a, const ProblemDev &P, int j,
-                                             bool exact, unsigned long long *xmax_s) {
+                                             const int32_t (&rows)[DMAX], bool exact,
+                                             unsigned long long *xmax_s) {
     const int d = P.d;
-    int32_t rows[DMAX];
+    unsigned long long v[DMAX];
 #pragma unroll
-    for (int t = 0; t < DMAX; ++t) rows[t] = (t < d) ? __ldg(P.csc_rows + (size_t)j * d + t) : 0;
+    for (int t = 0; t < DMAX; ++t) v[t] = (t < d) ? value_bits(__ldcg(P.r + rows[t])) : 0ull;
+    double xj = 0.0;
+    uint8_t ins = 1;
+    if (kCandidate) {
+        xj = __ldcg(P.x_hat + j);
+        if (!exact) ins = __ldcg(P.in_slots + j);
+    }
+    if (kPrefilter && !values_may_accept<DMAX>(v, d, a.alpha, a.mode)) return false;
     unsigned long long omega;
-    const bool acc = exact_score<DMAX, kPrefilter>(rows, d, P.r, a.alpha, a.mode, &omega);
+    const bool acc = exact_score_values<DMAX>(v, d, a.alpha, a.mode, &omega);
     if (acc) {
-        if (exact) apply_exact<DMAX>(P, j, rows, d, omega, __ldcg(P.x_hat + j), xmax_s);
-        else apply_pair<DMAX>(P, j, rows, d, omega);
+        if (!kCandidate) {
+            xj = __ldcg(P.x_hat + j);
+            if (!exact) ins = __ldcg(P.in_slots + j);
+        }
+        if (exact) apply_exact<DMAX>(P, j, rows, d, omega, xj, xmax_s);
+        else apply_pair_loaded<DMAX>(P, j, rows, d, omega, xj, ins);
     }
     return acc;
 }
@@ -437,7 +453,7 @@ __device__ __forceinline__ bool queue_or_score(const EngineArgs &a, const Proble
         for (int t = 0; t < DMAX; ++t) e[1 + t] = rows[t];
         return false;
     }
-    return score_inline<DMAX, THREADS != 1024>(a, P, j, exact, xmax_s);
+    return score_inline<DMAX, false, true>(a, P, j, rows, exact, xmax_s);
 }
 
 // The fingerprint test, then queue (or inline exact score), of up to 32
@@ -519,7 +535,7 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
             }
             bool acc = false;
             if (!use_fp) {
-                if (live) acc = score_inline<DMAX, THREADS != 1024>(a, P, j, exact, S.xmax);
+                if (live) acc = score_inline<DMAX, THREADS != 1024, false>(a, P, j, rows, exact, S.xmax);
             } else {
                 // the fingerprint bound: enough nonzero rows for the score
                 // (zero count), then a nonzero pair, then, only when the
