@@ -305,6 +305,52 @@ def undersampling_sweep(ccs, dev, reps: int, peak: float, seed: int):
     return {"reps": reps, "l2": "flushed before every decode (512 MB write)", "points": out}
 
 
+def alpha_sweep(ccs, dev, seed: int, reps: int = 3):
+    """The same n = 2^20 problem decoded with every alpha in [2, d] under both
+    scores: the l0 decrease of Eq. (15) and the match count of Alg. 8 (whose
+    alpha = floor(d/2) + 1 is Parallel-LDDSR, Sec. 4.3.2).  Per setting:
+    decodes/s (CUDA events, L2 flushed before each), iterations, outcome."""
+    import numpy as np
+    import torch
+
+    from paper_1508_01256_gb300 import inputs
+    p = inputs.plain_at_scale(seed=seed)
+    csc, ptr, cols = ccs.make_expander(p.n, p.m, p.d, p.a_seed, device=dev)
+    y = ccs.measure(ptr, cols, torch.from_numpy(p.x).to(dev), p.m, p.d)
+    ws = ccs.workspace(ccs.ccs_workspace_size(ccs.OP_DECODE, p.n, p.m, p.d), dev)
+    x_hat = torch.empty(p.n, dtype=torch.float64, device=dev)
+    r = torch.empty(p.m, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    names = {ccs.CONVERGED: "converged", ccs.STALLED: "stalled", ccs.MAX_ITER: "max_iter"}
+    out = []
+    for mode, mode_name in ((ccs.SCORE_L0_DECREASE, "l0_decrease"), (ccs.SCORE_COUNT, "count")):
+        for alpha in range(2, p.d + 1):
+            prm = ccs.params(alpha=alpha, score_mode=mode)
+            res_dev = ccs.result_buffer(reps + 1, dev)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(reps)]
+            for t in range(reps + 1):
+                flush.zero_()
+                if t > 0:
+                    evs[t - 1][0].record(stream)
+                ccs.ccs_decode_parallel_l0_async(p.n, p.m, p.d, csc, ptr, cols, y, x_hat, r,
+                                                 None, prm, res_dev[t * ccs.RESULT_BYTES:], ws,
+                                                 stream)
+                if t > 0:
+                    evs[t - 1][1].record(stream)
+            torch.cuda.synchronize()
+            last = ccs.results_from_device(res_dev, reps + 1)[-1]
+            ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+            out.append({"score": mode_name, "alpha": alpha,
+                        "parallel_lddsr": mode == ccs.SCORE_COUNT and alpha == p.d // 2 + 1,
+                        "decodes_per_s": 1000.0 / ms, "iterations": last.iterations,
+                        "status": names.get(last.status, last.status),
+                        "exact_recovery": bool(last.status == ccs.CONVERGED and
+                                               np.array_equal(x_hat.cpu().numpy(), p.x))})
+    return {"workload": f"n={p.n}, m={p.m}, d={p.d}, k={p.k}, gauss-grid", "points": out}
+
+
 def batched_vs_plain(ccs, dev, count: int, seed: int, reps: int = 3):
     """Decodes/s of `count` mixed problems (n log-uniform in [2^12, 2^20],
     delta, rho, d drawn from the batched workload's sets) in ONE persistent
@@ -646,6 +692,9 @@ def run_ccs(args):
     serving = None
     if args.serve > 0:
         serving = serving_run(ccs, dev, args.serve, seed=1000 * rank + 777)
+    alphas = None
+    if args.alpha_sweep > 0:
+        alphas = alpha_sweep(ccs, dev, seed=1000 * rank + 31)
     sweep = None
     if args.undersampling > 0:
         sweep = undersampling_sweep(ccs, dev, args.undersampling, measured_peaks()[0],
@@ -677,6 +726,7 @@ def run_ccs(args):
                 "batched": batched,
                 "serving": serving,
                 "undersampling": sweep,
+                "alpha_sweep": alphas,
                 "wall_s_timed_region": wall}
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -700,6 +750,8 @@ def main():
                     help="problems in the batched-vs-plain comparison (0: skip)")
     ap.add_argument("--serve", type=int, default=256,
                     help="requests in the serving run (0: skip)")
+    ap.add_argument("--alpha-sweep", type=int, default=1,
+                    help="alpha in [2, d] under both scores at n = 2^20 (0: skip)")
     ap.add_argument("--undersampling", type=int, default=3,
                     help="timed decodes per point of the n/m ~ 10^3 sweep (0: skip)")
     args = ap.parse_args()

@@ -76,12 +76,13 @@ def lib():
             l.oracle_l0.argtypes = [i32, _P]
             l.oracle_l0.restype = i64
             l.oracle_score_column.argtypes = [i32, _P, _P, i32, i32, _P, _P, _P]
-            l.oracle_score_all.argtypes = [i32, i32, _P, _P, i32, i32, _P, _P, _P]
+            l.oracle_score_column_shifted.argtypes = [i32, _P, _P, i32, i32, i32, _P, _P, _P]
+            l.oracle_score_all.argtypes = [i32, i32, _P, _P, i32, i32, i32, _P, _P, _P]
             l.oracle_score_all.restype = i64
-            l.oracle_parallel_l0.argtypes = [i32, i32, i32, _P, _P, i32, i32, i32,
+            l.oracle_parallel_l0.argtypes = [i32, i32, i32, _P, _P, i32, i32, i32, i32,
                                              _P, _P, _P, TRACE_FN, _P,
                                              ctypes.POINTER(Outcome)]
-            l.oracle_serial_l0.argtypes = [i32, i32, i32, _P, _P, i32, i32, i32,
+            l.oracle_serial_l0.argtypes = [i32, i32, i32, _P, _P, i32, i32, i32, i32,
                                            _P, _P, _P, ctypes.POINTER(Outcome)]
             _lib = l
     return _lib
@@ -153,22 +154,39 @@ def score_column(values_rows: np.ndarray, r: np.ndarray, alpha: int = 2,
     return bool(acc), om.value, sc.value, ct.value
 
 
+def score_column_shifted(values_rows: np.ndarray, r: np.ndarray, pos: int, alpha: int = 2,
+                         score_mode: int = SCORE_L0_DECREASE):
+    """Shifted score (Sec. 4.3.1): the candidate is r at row pos of the column."""
+    rows = np.ascontiguousarray(values_rows, dtype=np.int32)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    om = ctypes.c_double()
+    sc = ctypes.c_int32()
+    ct = ctypes.c_int32()
+    acc = lib().oracle_score_column_shifted(rows.size, _ptr(rows), _ptr(r), pos, alpha,
+                                            score_mode, ctypes.byref(om), ctypes.byref(sc),
+                                            ctypes.byref(ct))
+    if acc < 0:
+        raise ValueError("oracle_score_column_shifted: bad arguments")
+    return bool(acc), om.value, sc.value, ct.value
+
+
 def score_all(csc_rows: np.ndarray, r: np.ndarray, alpha: int = 2,
-              score_mode: int = SCORE_L0_DECREASE):
+              score_mode: int = SCORE_L0_DECREASE, shift_pos: int = -1):
     n, d = csc_rows.shape
     acc = np.empty(n, dtype=np.uint8)
     om = np.empty(n, dtype=np.float64)
     sc = np.empty(n, dtype=np.int32)
     lib().oracle_score_all(n, d, _ptr(np.ascontiguousarray(csc_rows)),
                            _ptr(np.ascontiguousarray(r, dtype=np.float64)), alpha,
-                           score_mode, _ptr(acc), _ptr(om), _ptr(sc))
+                           score_mode, shift_pos, _ptr(acc), _ptr(om), _ptr(sc))
     return acc.astype(bool), om, sc
 
 
 def parallel_l0(csc_rows: np.ndarray, m: int, y: np.ndarray, alpha: int = 2,
                 max_iter: int = 100, score_mode: int = SCORE_L0_DECREASE,
-                trace: bool = False):
-    """Alg. 2.  Returns dict(x_hat, r, r0_hist, status, iterations, r0_final[, trace])."""
+                trace: bool = False, shifted: bool = False):
+    """Alg. 2 (shifted: the variant of Sec. 4.3.1).  Returns dict(x_hat, r,
+    r0_hist, status, iterations, r0_final[, trace])."""
     n, d = csc_rows.shape
     x_hat = np.empty(n, dtype=np.float64)
     r = np.empty(m, dtype=np.float64)
@@ -185,8 +203,8 @@ def parallel_l0(csc_rows: np.ndarray, m: int, y: np.ndarray, alpha: int = 2,
     cb = TRACE_FN(_cb) if trace else TRACE_FN()
     rc = lib().oracle_parallel_l0(n, m, d, _ptr(np.ascontiguousarray(csc_rows)),
                                   _ptr(np.ascontiguousarray(y, dtype=np.float64)),
-                                  alpha, max_iter, score_mode, _ptr(x_hat), _ptr(r),
-                                  _ptr(hist), cb, None, ctypes.byref(out))
+                                  alpha, max_iter, score_mode, int(shifted), _ptr(x_hat),
+                                  _ptr(r), _ptr(hist), cb, None, ctypes.byref(out))
     if rc:
         raise ValueError(f"oracle_parallel_l0 failed ({rc})")
     res = dict(x_hat=x_hat, r=r, r0_hist=hist[:out.iterations + 1].copy(),
@@ -197,7 +215,8 @@ def parallel_l0(csc_rows: np.ndarray, m: int, y: np.ndarray, alpha: int = 2,
 
 
 def serial_l0(csc_rows: np.ndarray, m: int, y: np.ndarray, alpha: int = 2,
-              max_iter: int = 100, score_mode: int = SCORE_L0_DECREASE):
+              max_iter: int = 100, score_mode: int = SCORE_L0_DECREASE,
+              shifted: bool = False):
     """Alg. 1, one sweep over j = 0..n-1 per iteration."""
     n, d = csc_rows.shape
     x_hat = np.empty(n, dtype=np.float64)
@@ -206,8 +225,8 @@ def serial_l0(csc_rows: np.ndarray, m: int, y: np.ndarray, alpha: int = 2,
     out = Outcome()
     rc = lib().oracle_serial_l0(n, m, d, _ptr(np.ascontiguousarray(csc_rows)),
                                 _ptr(np.ascontiguousarray(y, dtype=np.float64)),
-                                alpha, max_iter, score_mode, _ptr(x_hat), _ptr(r),
-                                _ptr(hist), ctypes.byref(out))
+                                alpha, max_iter, score_mode, int(shifted), _ptr(x_hat),
+                                _ptr(r), _ptr(hist), ctypes.byref(out))
     if rc:
         raise ValueError(f"oracle_serial_l0 failed ({rc})")
     return dict(x_hat=x_hat, r=r, r0_hist=hist[:out.iterations + 1].copy(),

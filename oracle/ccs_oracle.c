@@ -223,16 +223,53 @@ int oracle_score_column(int32_t d, const int32_t *rows, const double *r,
     return *score >= alpha;
 }
 
-/* One score pass over all columns, all reading the same r. */
+/* Score of one column in the shifted variant (Sec. 4.3.1, the theorem on
+ * shifted Parallel-l0): the only candidate is omega = the value of r at the
+ * pos-th row of N(j) (rows ascending, pos counted from 0; reading R11); its
+ * count c_omega = #{t : r_{N(j)_t} = omega}, the score as in the other
+ * variant.  A zero candidate is never accepted (adding 0 changes nothing).
+ * Writes *omega, *score, *count as oracle_score_column. */
+int oracle_score_column_shifted(int32_t d, const int32_t *rows, const double *r,
+                                int32_t pos, int32_t alpha, int32_t score_mode,
+                                double *omega, int32_t *score, int32_t *count)
+{
+    if (d < 1 || d > 64 || pos < 0 || pos >= d) return -1;
+    const double w = r[rows[pos]];
+    int c0 = 0, c = 0;
+    for (int t = 0; t < d; ++t) {
+        const double v = r[rows[t]];
+        if (v == 0.0) ++c0;
+        if (v == w) ++c;
+    }
+    if (w == 0.0) {
+        *omega = 0.0;
+        *count = 0;
+        *score = (score_mode == ORACLE_SCORE_COUNT) ? 0 : -c0;
+        return 0;
+    }
+    *omega = w;
+    *count = c;
+    *score = (score_mode == ORACLE_SCORE_COUNT) ? c : c - c0;
+    return *score >= alpha;
+}
+
+/* One score pass over all columns, all reading the same r.  shift_pos < 0:
+ * the mode of the nonzero values (Alg. 2); else the shifted candidate at
+ * that position. */
 int64_t oracle_score_all(int32_t n, int32_t d, const int32_t *csc_rows,
                          const double *r, int32_t alpha, int32_t score_mode,
-                         uint8_t *accept, double *omega, int32_t *score)
+                         int32_t shift_pos, uint8_t *accept, double *omega,
+                         int32_t *score)
 {
     int64_t accepted = 0;
     for (int64_t j = 0; j < n; ++j) {
         int32_t cnt;
-        int a = oracle_score_column(d, csc_rows + j * d, r, alpha, score_mode,
-                                    &omega[j], &score[j], &cnt);
+        int a = (shift_pos < 0)
+                    ? oracle_score_column(d, csc_rows + j * d, r, alpha, score_mode,
+                                          &omega[j], &score[j], &cnt)
+                    : oracle_score_column_shifted(d, csc_rows + j * d, r, shift_pos,
+                                                  alpha, score_mode, &omega[j],
+                                                  &score[j], &cnt);
         accept[j] = (uint8_t)a;
         accepted += a;
     }
@@ -253,9 +290,10 @@ static int check_params(int32_t d, int32_t alpha, int32_t max_iter,
     return 0;
 }
 
+/* shifted != 0: the shifted variant, candidate position = iteration mod d. */
 int oracle_parallel_l0(int32_t n, int32_t m, int32_t d, const int32_t *csc_rows,
                        const double *y, int32_t alpha, int32_t max_iter,
-                       int32_t score_mode, double *x_hat, double *r,
+                       int32_t score_mode, int32_t shifted, double *x_hat, double *r,
                        int64_t *r0_hist, oracle_trace_fn trace, void *trace_ctx,
                        oracle_outcome *out)
 {
@@ -284,7 +322,7 @@ int oracle_parallel_l0(int32_t n, int32_t m, int32_t d, const int32_t *csc_rows,
         if (it == max_iter) { status = ORACLE_MAX_ITER; break; }
         /* T <- {(j, omega_j) : ||r||_0 - ||r - omega_j a_j||_0 >= alpha} */
         int64_t accepted = oracle_score_all(n, d, csc_rows, r, alpha, score_mode,
-                                            accept, omega, score);
+                                            shifted ? it % d : -1, accept, omega, score);
         if (accepted == 0) { status = ORACLE_STALLED; break; }
         if (trace) trace(trace_ctx, it, n, accept, omega);
         /* for (j, omega_j) in T: x_hat_j <- x_hat_j + omega_j */
@@ -314,7 +352,7 @@ done:
  * (the normalisation by n of Sec. 5). */
 int oracle_serial_l0(int32_t n, int32_t m, int32_t d, const int32_t *csc_rows,
                      const double *y, int32_t alpha, int32_t max_iter,
-                     int32_t score_mode, double *x_hat, double *r,
+                     int32_t score_mode, int32_t shifted, double *x_hat, double *r,
                      int64_t *r0_hist, oracle_outcome *out)
 {
     if (check_params(d, alpha, max_iter, score_mode)) return -1;
@@ -338,9 +376,12 @@ int oracle_serial_l0(int32_t n, int32_t m, int32_t d, const int32_t *csc_rows,
             const int32_t *rows = csc_rows + j * d;
             double omega;
             int32_t score, cnt;
-            if (!oracle_score_column(d, rows, r, alpha, score_mode, &omega,
-                                     &score, &cnt))
-                continue;
+            const int a = shifted ? oracle_score_column_shifted(d, rows, r, it % d, alpha,
+                                                                score_mode, &omega, &score,
+                                                                &cnt)
+                                  : oracle_score_column(d, rows, r, alpha, score_mode,
+                                                        &omega, &score, &cnt);
+            if (!a) continue;
             x_hat[j] = x_hat[j] + omega;
             for (int t = 0; t < d; ++t) {
                 int64_t i = rows[t];

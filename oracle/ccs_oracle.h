@@ -37,17 +37,21 @@ int64_t oracle_l0(int32_t m, const double *r);
 int oracle_score_column(int32_t d, const int32_t *rows, const double *r,
                         int32_t alpha, int32_t score_mode, double *omega,
                         int32_t *score, int32_t *count);
+int oracle_score_column_shifted(int32_t d, const int32_t *rows, const double *r,
+                                int32_t pos, int32_t alpha, int32_t score_mode,
+                                double *omega, int32_t *score, int32_t *count);
 int64_t oracle_score_all(int32_t n, int32_t d, const int32_t *csc_rows,
                          const double *r, int32_t alpha, int32_t score_mode,
-                         uint8_t *accept, double *omega, int32_t *score);
+                         int32_t shift_pos, uint8_t *accept, double *omega,
+                         int32_t *score);
 int oracle_parallel_l0(int32_t n, int32_t m, int32_t d, const int32_t *csc_rows,
                        const double *y, int32_t alpha, int32_t max_iter,
-                       int32_t score_mode, double *x_hat, double *r,
+                       int32_t score_mode, int32_t shifted, double *x_hat, double *r,
                        int64_t *r0_hist, oracle_trace_fn trace, void *trace_ctx,
                        oracle_outcome *out);
 int oracle_serial_l0(int32_t n, int32_t m, int32_t d, const int32_t *csc_rows,
                      const double *y, int32_t alpha, int32_t max_iter,
-                     int32_t score_mode, double *x_hat, double *r,
+                     int32_t score_mode, int32_t shifted, double *x_hat, double *r,
                      int64_t *r0_hist, oracle_outcome *out);
 
 #ifdef __cplusplus

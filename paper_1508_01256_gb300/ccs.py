@@ -260,6 +260,13 @@ def ccs_decode_batch_async(probs, p: Params | None, out_dev, ws, stream=None):
     _check(rc, "ccs_decode_batch_async")
 
 
+def lddsr_alpha(d: int) -> int:
+    """Parallel-LDDSR (Sec. 4.3.2): LDDSR accepts (j, omega) when more than d/2
+    of j's rows hold omega; with the match-count score (Alg. 8) that is
+    alpha = floor(d/2) + 1 and score_mode = SCORE_COUNT."""
+    return d // 2 + 1
+
+
 def ccs_autotune(probs, p: Params | None, ws, stream=None) -> list:
     """Time every launch shape per launch group of this batch and record the
     fastest in the library's table; returns the shape picked per group."""

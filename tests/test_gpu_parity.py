@@ -158,6 +158,27 @@ def test_decode_all_d_and_modes(ccs, orc, d, mode):
         assert_same_decode(g, ref)
 
 
+@pytest.mark.parametrize("d", [5, 7, 9, 12])
+def test_parallel_lddsr_matches_oracle(ccs, orc, d):
+    """Parallel-LDDSR (Sec. 4.3.2): match-count score, alpha = floor(d/2) + 1,
+    on a problem in the regime where it recovers (small rho)."""
+    p = inputs.make_problem(40000, 4000, d, 120, 70 + d)
+    g, ref = _decode_both(ccs, orc, p, alpha=ccs.lddsr_alpha(d), score_mode=ccs.SCORE_COUNT)
+    assert_same_decode(g, ref)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_alpha_sweep_at_scale(ccs, orc, mode):
+    """Every alpha in [2, d] at n = 2^20 (the bench's alpha sweep)."""
+    p = inputs.plain_at_scale(seed=23)
+    csc, ptr, cols, y = device_problem(ccs, p)
+    A, y_ref = oracle_problem(orc, p)
+    for alpha in range(2, p.d + 1):
+        g = ccs.decode_parallel_l0(csc, ptr, cols, y, alpha=alpha, score_mode=mode, max_iter=30)
+        assert_same_decode(g, orc.parallel_l0(A, p.m, y_ref, alpha=alpha, score_mode=mode,
+                                              max_iter=30))
+
+
 def test_first_iteration_is_the_score_step(ccs, orc):
     """max_iter = 1: x_hat equals omega_j on the accepted columns of one score
     pass over r = y (Eq. (15) with the tie rule), zero elsewhere."""

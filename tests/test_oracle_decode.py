@@ -134,6 +134,17 @@ def test_theorem_regime(orc, q, k, seed):
     ser = orc.serial_l0(A, m, y, alpha=alpha, max_iter=50)
     assert ser["status"] == orc.CONVERGED and np.array_equal(ser["x_hat"], x)
     assert ser["iterations"] <= res["iterations"]
+    # the shifted variants (Sec. 4.3.1) recover x too (their theorem: same
+    # graphs, alpha = (1 - 2 eps) d); every pair they accept is (j, x_j)
+    shp = orc.parallel_l0(A, m, y, alpha=alpha, max_iter=50 * d, trace=True, shifted=True)
+    assert shp["status"] == orc.CONVERGED and np.array_equal(shp["x_hat"], x)
+    xh = np.zeros(n)
+    for it, idx, om in shp["trace"]:
+        for j, w in zip(idx, om):
+            assert xh[j] == 0.0 and w == x[j]
+        xh[idx] += om
+    shs = orc.serial_l0(A, m, y, alpha=alpha, max_iter=50 * d, shifted=True)
+    assert shs["status"] == orc.CONVERGED and np.array_equal(shs["x_hat"], x)
 
 
 def test_k0_converges_immediately(orc):
@@ -237,3 +248,18 @@ def test_small_workload_recovers(orc):
         res = orc.parallel_l0(A, p.m, y)
         assert res["status"] == orc.CONVERGED and np.array_equal(res["x_hat"], p.x)
         assert res["iterations"] <= math.ceil(math.log(41)) + 1
+
+
+def test_shifted_k1_single_iteration(orc):
+    """k = 1: at iteration 0 the shifted candidate of the support column is
+    x_j itself (all its rows hold it), score d; a column sharing o rows with
+    it has candidate x_j only when its first row is shared (score 2o - d in
+    the l0 form) else 0, so with alpha = d only the support column is taken:
+    one iteration, exact recovery."""
+    A = orc.make_expander(2000, 300, 7, 9)
+    x = np.zeros(2000)
+    x[777] = 1.25
+    y = orc.measure(A, 300, x)
+    res = orc.parallel_l0(A, 300, y, alpha=7, shifted=True)
+    assert res["status"] == orc.CONVERGED and res["iterations"] == 1
+    assert np.array_equal(res["x_hat"], x)

@@ -84,3 +84,35 @@ def test_score_hand_built_columns(orc):
     r = np.array([-0.0, 0.0, 4.0, 4.0, 4.0, 1.0, 1.0])
     acc, om, sc, ct = orc.score_column(rows, r)
     assert not acc and om == 4.0 and sc == 1 and ct == 3
+
+
+@pytest.mark.parametrize("d", [1, 3, 5, 7, 9, 16])
+@pytest.mark.parametrize("count_mode", [False, True])
+def test_shifted_score_matches_literal_definition(orc, d, count_mode):
+    """Shifted variant (Sec. 4.3.1): the candidate is r at the pos-th row of
+    N(j) (rows ascending); its score is checked against the literal
+    ||r||_0 - ||r - omega a_j||_0 on the whole vector (or the match count),
+    and a zero candidate is never accepted."""
+    rng = np.random.default_rng(100 + d * 7 + count_mode)
+    n, m = 300, 40
+    A = orc.make_expander(n, m, d, 55 + d)
+    assert np.all(np.diff(A, axis=1) > 0)  # rows ascending within a column
+    mode = orc.SCORE_COUNT if count_mode else orc.SCORE_L0_DECREASE
+    for trial in range(5):
+        r = _random_residual(rng, m, nvals=2 + trial)
+        for pos in range(d):
+            for alpha in (2, max(2, d)):
+                acc, om, sc = orc.score_all(A, r, alpha, mode, shift_pos=pos)
+                for j in range(n):
+                    w = float(r[A[j][pos]])
+                    a_j = np.zeros(m)
+                    a_j[A[j]] = 1.0
+                    if w == 0.0:
+                        assert not acc[j]
+                        continue
+                    lit = int(np.sum(r[A[j]] == w)) if count_mode else \
+                        _l0(r) - _l0(r - w * a_j)
+                    assert om[j] == w and sc[j] == lit
+                    assert bool(acc[j]) == (lit >= alpha)
+                    a1, w1, s1, _ = orc.score_column_shifted(A[j], r, pos, alpha, mode)
+                    assert (a1, w1, s1) == (bool(acc[j]), w, lit)
