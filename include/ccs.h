@@ -112,7 +112,13 @@ typedef struct {
                              chunk (d <= 8 only); 2 = 512 threads, two
                              tiles per warp and chunk; 3 = 768 threads, one
                              tile per warp and chunk (d <= 8 only)          */
-    int32_t reserved;     /* must be zero                                     */
+    int32_t shifted;      /* 0: Alg. 2, each column's candidate is the mode of
+                             its nonzero residual values.  1: the shifted
+                             variant of Sec. 4.3.1: at iteration l the only
+                             candidate is the value of r at the (l mod d)-th
+                             row of the column (rows ascending, counted from
+                             0); O(d) per column for any alpha.  Persistent
+                             engine only.  Default 0.                        */
 } ccs_params;
 
 typedef struct {

@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("score_mode", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("watchdog_ms", ctypes.c_int32), ("debug_flags", ctypes.c_int32),
-                ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32), ("shifted", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -197,12 +197,13 @@ def _need(t, dtype, numel, name):
 
 
 def params(alpha=2, max_iter=100, score_mode=SCORE_L0_DECREASE, engine=ENGINE_AUTO,
-           watchdog_ms=0, debug_flags=0, schedule=0) -> Params:
+           watchdog_ms=0, debug_flags=0, schedule=0, shifted=False) -> Params:
     p = Params()
     lib().ccs_params_init(ctypes.byref(p))
     p.alpha, p.max_iter, p.score_mode, p.engine, p.watchdog_ms, p.debug_flags = (
         alpha, max_iter, score_mode, engine, watchdog_ms, debug_flags)
     p.schedule = schedule
+    p.shifted = int(shifted)
     return p
 
 
@@ -384,7 +385,7 @@ class DecodeOutput(dict):
 def decode_parallel_l0(csc_rows, csr_ptr, csr_cols, y, alpha=2, max_iter=100,
                        score_mode=SCORE_L0_DECREASE, engine=ENGINE_AUTO, history=True,
                        ws=None, out=None, stream=None, watchdog_ms=0,
-                       debug_flags=0, schedule=0) -> DecodeOutput:
+                       debug_flags=0, schedule=0, shifted=False) -> DecodeOutput:
     """Parallel-l0 (Alg. 2) on one problem; returns x_hat, r (device tensors),
     r0_hist (host list), status, iterations, r0_final."""
     import torch
@@ -403,7 +404,7 @@ def decode_parallel_l0(csc_rows, csr_ptr, csr_cols, y, alpha=2, max_iter=100,
         x_hat, r, hist = out
     if ws is None:
         ws = workspace(ccs_workspace_size(OP_DECODE, n, m, d), dev)
-    p = params(alpha, max_iter, score_mode, engine, watchdog_ms, debug_flags, schedule)
+    p = params(alpha, max_iter, score_mode, engine, watchdog_ms, debug_flags, schedule, shifted)
     res = ccs_decode_parallel_l0(n, m, d, csc_rows, csr_ptr, csr_cols, y, x_hat, r, hist, p,
                                  ws, stream)
     h = hist[:res.iterations + 1].cpu().tolist() if hist is not None else None
@@ -418,7 +419,8 @@ def problem(csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist=None) -> Problem:
 
 
 def decode_batch(items, alpha=2, max_iter=100, score_mode=SCORE_L0_DECREASE,
-                 engine=ENGINE_AUTO, history=False, ws=None, stream=None, debug_flags=0):
+                 engine=ENGINE_AUTO, history=False, ws=None, stream=None, debug_flags=0,
+                 shifted=False):
     """items: list of (csc_rows, csr_ptr, csr_cols, y).  Returns a list of
     DecodeOutput, one per problem, from a single ccs_decode_batch call."""
     import torch
@@ -434,7 +436,7 @@ def decode_batch(items, alpha=2, max_iter=100, score_mode=SCORE_L0_DECREASE,
         probs.append(problem(csc, ptr, cols, y, x_hat, r, hist))
     if ws is None:
         ws = workspace(ccs_batch_workspace_size(probs), items[0][3].device)
-    p = params(alpha, max_iter, score_mode, engine, debug_flags=debug_flags)
+    p = params(alpha, max_iter, score_mode, engine, debug_flags=debug_flags, shifted=shifted)
     res = ccs_decode_batch(probs, p, ws, stream)
     result = []
     for (x_hat, r, hist), rr in zip(outs, res):

@@ -175,8 +175,16 @@ int check_params(const ccs_params *p, int d) {
         set_last_error("unknown engine %d", p->engine);
         return CCS_EINVAL;
     }
-    if (p->watchdog_ms < 0 || p->reserved || p->schedule < 0 || p->schedule > 3) {
-        set_last_error("bad watchdog_ms, schedule or nonzero reserved field");
+    if (p->watchdog_ms < 0 || p->schedule < 0 || p->schedule > 3) {
+        set_last_error("bad watchdog_ms or schedule");
+        return CCS_EINVAL;
+    }
+    if (p->shifted != 0 && p->shifted != 1) {
+        set_last_error("shifted must be 0 or 1 (got %d)", p->shifted);
+        return CCS_EINVAL;
+    }
+    if (p->shifted && p->engine == CCS_ENGINE_HOST_LOOP) {
+        set_last_error("the shifted variant runs on the persistent engine only");
         return CCS_EINVAL;
     }
     return CCS_OK;

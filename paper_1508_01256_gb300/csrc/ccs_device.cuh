@@ -154,6 +154,27 @@ __device__ __forceinline__ bool exact_score_values(const unsigned long long (&v)
     return best_cnt > 0 && score >= alpha;
 }
 
+// Shifted variant (Sec. 4.3.1): the only candidate is v[pos], the value at
+// the pos-th row of the column (pos = iteration mod d); its count and score
+// as in exact_score_values.  A zero candidate is never accepted.
+template <int DMAX>
+__device__ __forceinline__ bool exact_score_shifted(const unsigned long long (&v)[DMAX], int d,
+                                                    int pos, int alpha, int mode,
+                                                    unsigned long long *omega) {
+    unsigned long long w = 0ull;
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t) w = (t == pos) ? v[t] : w;
+    int c0 = 0, c = 0;
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t) {
+        c0 += (t < d) & (v[t] == 0ull);
+        c += (t < d) & (v[t] == w);
+    }
+    *omega = w;
+    if (w == 0ull) return false;
+    return ((mode == CCS_SCORE_COUNT) ? c : c - c0) >= alpha;
+}
+
 // The fingerprint bound computed from gathered values v (value_bits form):
 // false when no value of the column can reach alpha (exact rejection: equal
 // values have equal fingerprints).  Cheaper than the O(d^2) compare of

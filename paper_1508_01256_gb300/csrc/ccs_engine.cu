@@ -280,6 +280,7 @@ static void fill_args(EngineArgs &a, const LaunchPlan &L, int P, const ccs_param
     a.queue_cap = L.queue_cap;
     a.watchdog_ns = (long long)(prm.watchdog_ms > 0 ? prm.watchdog_ms : 2000) * 1000000ll;
     a.debug_flags = prm.debug_flags;
+    a.shifted = prm.shifted;
     a.iter_budget = 0x7fffffff;
 }
 

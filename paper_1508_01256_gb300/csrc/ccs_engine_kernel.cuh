@@ -77,6 +77,7 @@ struct EngineArgs {
     ccs_result *dev_out;        // per-problem results in device memory (or null)
     int resume;                 // control blocks persist; only kPdFresh problems initialise
     int iter_budget;            // iterations this launch may run
+    int shifted;                // 1: the shifted variant (Sec. 4.3.1)
 };
 
 // ---- device helpers --------------------------------------------------------
@@ -358,7 +359,7 @@ __device__ __forceinline__ void issue_chunk(const EngineArgs &a, const ProblemDe
 template <int DMAX, bool kPrefilter, bool kCandidate>
 __device__ __forceinline__ bool score_inline(const EngineArgs &a, const ProblemDev &P, int j,
                                              const int32_t (&rows)[DMAX], bool exact,
-                                             unsigned long long *xmax_s) {
+                                             unsigned long long *xmax_s, int spos) {
     const int d = P.d;
     unsigned long long v[DMAX];
 #pragma unroll
@@ -369,9 +370,14 @@ __device__ __forceinline__ bool score_inline(const EngineArgs &a, const ProblemD
         xj = __ldcg(P.x_hat + j);
         if (!exact) ins = __ldcg(P.in_slots + j);
     }
-    if (kPrefilter && !values_may_accept<DMAX>(v, d, a.alpha, a.mode)) return false;
     unsigned long long omega;
-    const bool acc = exact_score_values<DMAX>(v, d, a.alpha, a.mode, &omega);
+    bool acc;
+    if (spos >= 0) {
+        acc = exact_score_shifted<DMAX>(v, d, spos, a.alpha, a.mode, &omega);
+    } else {
+        if (kPrefilter && !values_may_accept<DMAX>(v, d, a.alpha, a.mode)) return false;
+        acc = exact_score_values<DMAX>(v, d, a.alpha, a.mode, &omega);
+    }
     if (acc) {
         if (!kCandidate) {
             xj = __ldcg(P.x_hat + j);
@@ -389,7 +395,7 @@ template <int DMAX>
 __device__ __forceinline__ void score_queue(const EngineArgs &a, const ProblemDev &P,
                                          const int32_t *queue, int qn,
                                          unsigned long long *acc_smem, bool ok, bool exact,
-                                         unsigned long long *xmax_s) {
+                                         unsigned long long *xmax_s, int spos) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int d = P.d;
     for (int b0 = warp * 32; b0 < qn; b0 += blockDim.x) {
@@ -407,7 +413,8 @@ __device__ __forceinline__ void score_queue(const EngineArgs &a, const ProblemDe
             const double xj = __ldcg(P.x_hat + j);
             const uint8_t ins = __ldcg(P.in_slots + j);
             unsigned long long omega;
-            acc = exact_score_values<DMAX>(v, d, a.alpha, a.mode, &omega);
+            acc = (spos >= 0) ? exact_score_shifted<DMAX>(v, d, spos, a.alpha, a.mode, &omega)
+                              : exact_score_values<DMAX>(v, d, a.alpha, a.mode, &omega);
             if (acc) {
                 if (exact) apply_exact<DMAX>(P, j, rows, d, omega, xj, xmax_s);
                 else apply_pair_loaded<DMAX>(P, j, rows, d, omega, xj, ins);
@@ -444,7 +451,7 @@ template <int DMAX, int THREADS>
 __device__ __forceinline__ bool queue_or_score(const EngineArgs &a, const ProblemDev &P,
                                                int32_t *queue, int *qn, int j,
                                                const int32_t (&rows)[DMAX], bool exact,
-                                               unsigned long long *xmax_s) {
+                                               unsigned long long *xmax_s, int spos) {
     const int q = atomicAdd(qn, 1);
     if (q < a.queue_cap) {  // scored after the stream
         int32_t *e = queue + q * (DMAX + 1);
@@ -453,7 +460,7 @@ __device__ __forceinline__ bool queue_or_score(const EngineArgs &a, const Proble
         for (int t = 0; t < DMAX; ++t) e[1 + t] = rows[t];
         return false;
     }
-    return score_inline<DMAX, false, true>(a, P, j, rows, exact, xmax_s);
+    return score_inline<DMAX, false, true>(a, P, j, rows, exact, xmax_s, spos);
 }
 
 // The fingerprint test, then queue (or inline exact score), of up to 32
@@ -480,7 +487,7 @@ __device__ __noinline__ int flush_candidates(const EngineArgs &a, const ProblemD
         }
         const int need = (a.mode == CCS_SCORE_COUNT) ? a.alpha : a.alpha + (d - nz);
         if (fp_bound_passes<DMAX, kWide>(f, d, need))
-            acc = queue_or_score<DMAX, THREADS>(a, P, queue, qn, j, rows, exact, xmax_s);
+            acc = queue_or_score<DMAX, THREADS>(a, P, queue, qn, j, rows, exact, xmax_s, -1);
     }
     return __popc(__ballot_sync(0xffffffffu, acc));
 }
@@ -493,7 +500,7 @@ template <int DMAX, int THREADS, bool kExactD, bool kWide>
 __device__ __forceinline__ void consume_segment(const EngineArgs &a, const ProblemDev &P,
                                                 const Segment &sg, int per, int nchunks,
                                                 unsigned chunk_seq, ScoreSmem &S, int *wb,
-                                                bool exact, bool &ok) {
+                                                bool exact, int spos, bool &ok) {
     constexpr int kTpw = (THREADS == 512) ? 2 : 1;
     const int warps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -535,7 +542,9 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
             }
             bool acc = false;
             if (!use_fp) {
-                if (live) acc = score_inline<DMAX, THREADS != 1024, false>(a, P, j, rows, exact, S.xmax);
+                if (live)
+                    acc = score_inline<DMAX, THREADS != 1024, false>(a, P, j, rows, exact, S.xmax,
+                                                                     spos);
             } else {
                 // the fingerprint bound: enough nonzero rows for the score
                 // (zero count), then a nonzero pair, then, only when the
@@ -548,13 +557,27 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
                     nz += (f[t] != 0u);
                 }
                 const int need = (a.mode == CCS_SCORE_COUNT) ? a.alpha : a.alpha + (d - nz);
+                if (spos >= 0) {
+                    // shifted: the candidate's fingerprint count bounds its count
+                    unsigned fw = 0u;
+#pragma unroll
+                    for (int t = 0; t < DMAX; ++t) fw = (t == spos) ? f[t] : fw;
+                    int cf = 0;
+#pragma unroll
+                    for (int t = 0; t < DMAX; ++t) cf += (t < d) & (f[t] == fw);
+                    if (live && fw != 0u && nz >= need && cf >= need)
+                        acc = queue_or_score<DMAX, THREADS>(a, P, S.queue, S.qn, j, rows, exact,
+                                                            S.xmax, spos);
+                    n_acc += __popc(__ballot_sync(0xffffffffu, acc));
+                    continue;
+                }
                 const bool pass = live && nz >= need;
                 const unsigned bal = __ballot_sync(0xffffffffu, pass);
                 if (bal) {
                     if (!kUseWarpBuffer<THREADS, kWide> || __popc(bal) >= kDenseLanes) {
                         if (pass && fp_bound_passes<DMAX, kWide>(f, d, need))
                             acc = queue_or_score<DMAX, THREADS>(a, P, S.queue, S.qn, j, rows,
-                                                                exact, S.xmax);
+                                                                exact, S.xmax, -1);
                     } else if constexpr (kUseWarpBuffer<THREADS, kWide>) {
                         // append; a full buffer is tested right away and the
                         // lanes that did not fit start the next one
@@ -604,6 +627,7 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
                                               ScoreSmem &S, unsigned &chunk_seq,
                                               unsigned &fp_seq, bool &ok) {
     const bool exact = rmode == 0;
+    const int spos = a.shifted ? it % P.d : -1;  // shifted variant: candidate row
     const Segment sg{0, seg_lo, seg_hi, 0};
     const int warps = blockDim.x >> 5;
     constexpr int kTpw = (THREADS == 512) ? 2 : 1;  // tiles per consumer warp and chunk
@@ -669,14 +693,14 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
         const bool wide = fp16_for(P.m);
         if (P.d == DMAX) {
             if (wide)
-                consume_segment<DMAX, THREADS, true, true>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, ok);
+                consume_segment<DMAX, THREADS, true, true>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, spos, ok);
             else
-                consume_segment<DMAX, THREADS, true, false>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, ok);
+                consume_segment<DMAX, THREADS, true, false>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, spos, ok);
         } else {
             if (wide)
-                consume_segment<DMAX, THREADS, false, true>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, ok);
+                consume_segment<DMAX, THREADS, false, true>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, spos, ok);
             else
-                consume_segment<DMAX, THREADS, false, false>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, ok);
+                consume_segment<DMAX, THREADS, false, false>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, spos, ok);
         }
     }
     chunk_seq += nchunks;
@@ -685,7 +709,7 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
     if (a.stamps && blockIdx.x == 0 && threadIdx.x == 0 && g < kMaxStampIters)
         a.stamps[kSubBase + 3 * g + 1] = globaltimer();
 
-    score_queue<DMAX>(a, P, S.queue, min(*S.qn, a.queue_cap), S.acc, ok, exact, S.xmax);
+    score_queue<DMAX>(a, P, S.queue, min(*S.qn, a.queue_cap), S.acc, ok, exact, S.xmax, spos);
     // one global atomic per CTA and segment (all warps' counts summed on chip)
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -315,7 +315,7 @@ void ccs_params_init(ccs_params *p) {
     p->watchdog_ms = 0;
     p->debug_flags = 0;
     p->schedule = 0;
-    p->reserved = 0;
+    p->shifted = 0;
 }
 
 size_t ccs_workspace_size(int32_t op, int32_t n, int32_t m, int32_t d) {

@@ -69,7 +69,7 @@ def _decode_both(ccs, orc, p, **kw):
     csc, ptr, cols, y = device_problem(ccs, p)
     g = ccs.decode_parallel_l0(csc, ptr, cols, y, **kw)
     A, y_ref = oracle_problem(orc, p)
-    okw = {k: v for k, v in kw.items() if k in ("alpha", "max_iter", "score_mode")}
+    okw = {k: v for k, v in kw.items() if k in ("alpha", "max_iter", "score_mode", "shifted")}
     ref = orc.parallel_l0(A, p.m, y_ref, **okw)
     return g, ref
 
@@ -524,3 +524,39 @@ def test_autotune_records_a_shape_and_keeps_results(ccs, orc):
             assert_same_decode(g, orc.parallel_l0(A, p.m, y_ref))
     finally:
         ccs.ccs_autotune_reset()
+
+
+SHIFTED_CASES = [(4096, 410, 7, 41, 0), (6007, 700, 5, 70, 1), (20000, 2000, 9, 300, 0),
+                 (60001, 6000, 16, 500, 1), (2 ** 20, 2 ** 17, 7, 13107, 0)]
+
+
+@pytest.mark.parametrize("shape", SHIFTED_CASES)
+def test_shifted_matches_oracle(ccs, orc, shape):
+    """Shifted Parallel-l0 (Sec. 4.3.1): at iteration l the candidate of
+    each column is r at its (l mod d)-th row; bit-identical to the oracle."""
+    n, m, d, k, mode = shape
+    p = inputs.make_problem(n, m, d, k, 500 + d)
+    for alpha in sorted({2, d // 2 + 1, d}):
+        g, ref = _decode_both(ccs, orc, p, alpha=alpha, score_mode=mode, max_iter=60,
+                              shifted=True)
+        assert_same_decode(g, ref)
+
+
+def test_shifted_batch_and_residual_modes(ccs, orc):
+    """Shifted variant in a mixed batch, with the exact residual and with a
+    forced switch to the ordered residual."""
+    probs = inputs.batch_problems(10, seed=19, log2n_hi=15.0)
+    items = [device_problem(ccs, p) for p in probs]
+    for flags in (0, 4):
+        outs = ccs.decode_batch(items, history=True, shifted=True, debug_flags=flags)
+        for p, g in zip(probs, outs):
+            A, y_ref = oracle_problem(orc, p)
+            assert_same_decode(g, orc.parallel_l0(A, p.m, y_ref, shifted=True))
+
+
+def test_shifted_rejected_on_host_loop(ccs):
+    p = inputs.plain_small(seed=2)
+    csc, ptr, cols, y = device_problem(ccs, p)
+    with pytest.raises(ccs.CcsError) as ei:
+        ccs.decode_parallel_l0(csc, ptr, cols, y, engine=ccs.ENGINE_HOST_LOOP, shifted=True)
+    assert ei.value.code == ccs.CCS_EINVAL
