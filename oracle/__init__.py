@@ -71,6 +71,9 @@ def lib():
             l.oracle_splitmix64_next.restype = u64
             l.oracle_make_expander.argtypes = [i32, i32, i32, u64, _P]
             l.oracle_transpose.argtypes = [i32, i32, i32, _P, _P, _P]
+            l.oracle_column_scales.argtypes = [i32, u64, _P]
+            l.oracle_measure_scaled.argtypes = [i32, _P, _P, _P, _P, _P]
+            l.oracle_unscale.argtypes = [i32, _P, _P, _P]
             l.oracle_measure.argtypes = [i32, _P, _P, _P, _P]
             l.oracle_residual.argtypes = [i32, _P, _P, _P, _P, _P]
             l.oracle_l0.argtypes = [i32, _P]
@@ -124,6 +127,31 @@ def measure(csc_rows: np.ndarray, m: int, x: np.ndarray) -> np.ndarray:
     y = np.empty(m, dtype=np.float64)
     lib().oracle_measure(m, _ptr(ptr), _ptr(cols), _ptr(x), _ptr(y))
     return y
+
+
+def column_scales(n: int, seed: int) -> np.ndarray:
+    """Column scales of Sec. 4.3.3 (reading R12): s_j on [1, 2), grid 2^-20."""
+    s = np.empty(n, dtype=np.float64)
+    if lib().oracle_column_scales(n, ctypes.c_uint64(seed), _ptr(s)):
+        raise ValueError("oracle_column_scales: bad arguments")
+    return s
+
+
+def measure_scaled(csc_rows: np.ndarray, m: int, s: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """y = A diag(s) x, ordered row sums of the products s_j x_j."""
+    ptr, cols = transpose(csc_rows, m)
+    y = np.empty(m, dtype=np.float64)
+    lib().oracle_measure_scaled(m, _ptr(ptr), _ptr(cols),
+                                _ptr(np.ascontiguousarray(s, dtype=np.float64)),
+                                _ptr(np.ascontiguousarray(x, dtype=np.float64)), _ptr(y))
+    return y
+
+
+def unscale(s: np.ndarray, z: np.ndarray) -> np.ndarray:
+    x = np.empty(s.size, dtype=np.float64)
+    lib().oracle_unscale(s.size, _ptr(np.ascontiguousarray(s, dtype=np.float64)),
+                         _ptr(np.ascontiguousarray(z, dtype=np.float64)), _ptr(x))
+    return x
 
 
 def residual(csc_rows: np.ndarray, m: int, y: np.ndarray, x_hat: np.ndarray):

@@ -35,6 +35,14 @@
  *       distinct and uniform over the C(m, d) supports, drawn from the
  *       counter-based SplitMix64 stream of column j with Lemire's bounded
  *       draw, repeated rows redrawn, then sorted ascending.
+ *   R12 Column scaling for signals that are not dissociated (Sec. 4.3.3):
+ *       "scaling each column by i.i.d. random numbers from a continuous
+ *       distribution" is one scale s_j per column, uniform on [1, 2) to a
+ *       grid of 2^-20 (1 + the top 20 bits of the first draw of column j's
+ *       stream, times 2^-20), so that products with small integers and
+ *       their sums stay exact.  The scaled matrix A diag(s) measures
+ *       y = A (s . x); Parallel-l0 on A and y recovers z = s . x, and
+ *       x = z / s.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -117,6 +125,19 @@ int oracle_make_expander(int32_t n, int32_t m, int32_t d, uint64_t seed,
     return 0;
 }
 
+/* Column scales (reading R12): s_j = 1 + (first draw of column j's stream
+ * >> 44) * 2^-20. */
+int oracle_column_scales(int32_t n, uint64_t seed, double *s)
+{
+    if (n < 1 || !s) return -1;
+    for (int64_t j = 0; j < n; ++j) {
+        uint64_t state = column_stream_start(seed, j);
+        const uint64_t k = oracle_splitmix64_next(&state) >> 44;
+        s[j] = 1.0 + (double)k / 1048576.0;
+    }
+    return 0;
+}
+
 /* N(i) for every row i: the transpose of the CSC, columns ascending. */
 int oracle_transpose(int32_t n, int32_t m, int32_t d, const int32_t *csc_rows,
                      int64_t *csr_ptr, int32_t *csr_cols)
@@ -162,6 +183,30 @@ int oracle_measure(int32_t m, const int64_t *csr_ptr, const int32_t *csr_cols,
                    const double *x, double *y)
 {
     for (int64_t i = 0; i < m; ++i) y[i] = row_sum(csr_ptr, csr_cols, x, i);
+    return 0;
+}
+
+/* y = A diag(s) x (reading R12): y_i = ordered sum over j in N(i) of the
+ * nonzero products s_j * x_j (each product rounded once), from +0.0. */
+int oracle_measure_scaled(int32_t m, const int64_t *csr_ptr, const int32_t *csr_cols,
+                          const double *s, const double *x, double *y)
+{
+    for (int64_t i = 0; i < m; ++i) {
+        double acc = +0.0;
+        for (int64_t p = csr_ptr[i]; p < csr_ptr[i + 1]; ++p) {
+            const int32_t j = csr_cols[p];
+            const double v = s[j] * x[j];
+            if (v != 0.0) acc = acc + v;
+        }
+        y[i] = acc;
+    }
+    return 0;
+}
+
+/* x_j = z_j / s_j: the signal from the decode z of A diag(s)'s measurement. */
+int oracle_unscale(int32_t n, const double *s, const double *z, double *x)
+{
+    for (int64_t j = 0; j < n; ++j) x[j] = z[j] / s[j];
     return 0;
 }
 

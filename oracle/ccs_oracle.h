@@ -27,6 +27,10 @@ typedef void (*oracle_trace_fn)(void *ctx, int32_t iteration, int32_t n,
 uint64_t oracle_splitmix64_next(uint64_t *state);
 int oracle_make_expander(int32_t n, int32_t m, int32_t d, uint64_t seed,
                          int32_t *csc_rows);
+int oracle_column_scales(int32_t n, uint64_t seed, double *s);
+int oracle_measure_scaled(int32_t m, const int64_t *csr_ptr, const int32_t *csr_cols,
+                          const double *s, const double *x, double *y);
+int oracle_unscale(int32_t n, const double *s, const double *z, double *x);
 int oracle_transpose(int32_t n, int32_t m, int32_t d, const int32_t *csc_rows,
                      int64_t *csr_ptr, int32_t *csr_cols);
 int oracle_measure(int32_t m, const int64_t *csr_ptr, const int32_t *csr_cols,

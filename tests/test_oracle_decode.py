@@ -263,3 +263,59 @@ def test_shifted_k1_single_iteration(orc):
     res = orc.parallel_l0(A, 300, y, alpha=7, shifted=True)
     assert res["status"] == orc.CONVERGED and res["iterations"] == 1
     assert np.array_equal(res["x_hat"], x)
+
+
+def test_column_scales_grid_and_distribution(orc):
+    """Reading R12: s_j on [1, 2), multiples of 2^-20, close to uniform, and
+    a different sequence for another seed."""
+    s = orc.column_scales(200000, 5)
+    assert np.all((s >= 1.0) & (s < 2.0))
+    k = (s - 1.0) * 2 ** 20
+    assert np.array_equal(k, np.floor(k))
+    assert abs(s.mean() - 1.5) < 0.003 and abs(s.std() - (1 / 12) ** 0.5) < 0.003
+    hist = np.histogram(s, bins=16, range=(1.0, 2.0))[0]
+    assert hist.min() > 0.9 * 200000 / 16
+    assert not np.array_equal(s[:100], orc.column_scales(100, 6))
+
+
+def test_measure_scaled_is_the_exact_sum(orc):
+    """y = A diag(s) x on +/-1 and small-integer x equals the exact rational
+    sum (integer arithmetic on the 2^-20 grid)."""
+    n, m, d = 3000, 300, 7
+    A = orc.make_expander(n, m, d, 3)
+    s = orc.column_scales(n, 11)
+    rng = np.random.default_rng(4)
+    x = np.zeros(n)
+    supp = rng.choice(n, 200, replace=False)
+    x[supp] = rng.choice([-3.0, -1.0, 1.0, 2.0], 200)
+    y = orc.measure_scaled(A, m, s, x)
+    si = ((s - 1.0) * 2 ** 20).astype(np.int64) + 2 ** 20      # s_j * 2^20
+    exact = np.zeros(m, dtype=np.int64)
+    for j in supp:
+        for i in A[j]:
+            exact[i] += si[j] * int(x[j])
+    assert np.array_equal(y * 2 ** 20, exact.astype(np.float64))
+
+
+@pytest.mark.parametrize("q,k,seed", [(5, 3, 0), (7, 3, 1), (7, 4, 2)])
+def test_scaled_columns_recover_pm1_signals(orc, q, k, seed):
+    """Sec. 4.3.3: with every value of x equal to +1 (not dissociated: equal
+    values), scaling A's columns by i.i.d. continuous numbers lets
+    Parallel-l0 identify the support; decoding y = A (s . x) recovers
+    z = s . x exactly in the theorem regime, and z / s = x."""
+    rng = np.random.default_rng(300 + 10 * q + seed)
+    A = affine_plane(q)
+    perm = rng.permutation(q * q).astype(np.int32)
+    A = np.sort(perm[A], axis=1).astype(np.int32)
+    n, d = A.shape
+    m = q * q
+    es = eps_star(A, m, k)
+    alpha = math.ceil((1 - 2 * es) * d)
+    x = np.zeros(n)
+    x[np.sort(rng.choice(n, size=k, replace=False))] = 1.0
+    s = orc.column_scales(n, 1000 + seed)
+    y = orc.measure_scaled(A, m, s, x)
+    res = orc.parallel_l0(A, m, y, alpha=alpha, max_iter=50)
+    assert res["status"] == orc.CONVERGED
+    assert np.array_equal(res["x_hat"], s * x)
+    assert np.array_equal(orc.unscale(s, res["x_hat"]), x)
