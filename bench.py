@@ -247,7 +247,8 @@ def cpu_baseline(name: str, budget_s: float = 12.0):
 def undersampling_sweep(ccs, dev, reps: int, peak: float, seed: int):
     """n/m ~ 10^3 (Sec. 5.5 shape): n=2^24, m=16777, d=9, rho = 0.05..0.30 in
     six steps on gauss-grid values, the +/-1 (non-dissociated) variant at
-    rho=0.05, and d=7, rho=0.05 beside the paper's Table 3 time.  Each point:
+    rho=0.05 with and without column scaling (Sec. 4.3.3), and d=7,
+    rho=0.05 beside the paper's Table 3 time.  Each point:
     one untimed decode, then `reps` decodes with an L2 flush before each,
     timed with CUDA events on the launching stream.  The CSC alone (604 MB at
     d=9) is far larger than L2, so every iteration streams it from HBM."""
@@ -256,15 +257,24 @@ def undersampling_sweep(ccs, dev, reps: int, peak: float, seed: int):
 
     from paper_1508_01256_gb300 import inputs
     points = [(9, rho, "gauss-grid") for rho in (0.05, 0.10, 0.15, 0.20, 0.25, 0.30)]
-    points += [(9, 0.05, "pm1"), (7, 0.05, "gauss-grid")]
+    points += [(9, 0.05, "pm1"), (9, 0.05, "pm1-scaled"), (7, 0.05, "gauss-grid")]
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     names = {ccs.CONVERGED: "converged", ccs.STALLED: "stalled", ccs.MAX_ITER: "max_iter"}
     out = []
     for i, (d, rho, model) in enumerate(points):
-        p = inputs.extreme_undersampling(rho, d=d, seed=seed + i, model=model)
+        scaled = model.endswith("-scaled")
+        p = inputs.extreme_undersampling(rho, d=d, seed=seed + i,
+                                         model=model.replace("-scaled", ""))
         csc, ptr, cols = ccs.make_expander(p.n, p.m, p.d, p.a_seed, device=dev)
-        y = ccs.measure(ptr, cols, torch.from_numpy(p.x).to(dev), p.m, p.d)
+        x_dev = torch.from_numpy(p.x).to(dev)
+        if scaled:
+            # Sec. 4.3.3: A's columns scaled by i.i.d. numbers; the decode
+            # recovers z = s . x and x = z / s
+            sc = ccs.column_scales(p.n, seed + 1000 + i, dev)
+            y = ccs.measure_scaled(ptr, cols, sc, x_dev, p.m, p.d)
+        else:
+            y = ccs.measure(ptr, cols, x_dev, p.m, p.d)
         ws = ccs.workspace(ccs.ccs_workspace_size(ccs.OP_DECODE, p.n, p.m, p.d), dev)
         x_hat = torch.empty(p.n, dtype=torch.float64, device=dev)
         r = torch.empty(p.m, dtype=torch.float64, device=dev)
@@ -287,11 +297,12 @@ def undersampling_sweep(ccs, dev, reps: int, peak: float, seed: int):
         it = last.iterations
         alg = it * (4 * p.d * p.n + 8 * p.m)
         gbs = alg / (ms * 1e-3) / 1e9
-        entry = {"n": p.n, "m": p.m, "d": p.d, "k": p.k, "rho": rho, "values": p.model,
+        x_out = ccs.unscale(sc, x_hat) if scaled else x_hat
+        entry = {"n": p.n, "m": p.m, "d": p.d, "k": p.k, "rho": rho, "values": model,
                  "ms_per_decode": ms, "decodes_per_s": 1000.0 / ms, "iterations": it,
                  "status": names.get(last.status, last.status),
                  "exact_recovery": bool(last.status == ccs.CONVERGED and
-                                        np.array_equal(x_hat.cpu().numpy(), p.x)),
+                                        np.array_equal(x_out.cpu().numpy(), p.x)),
                  "same_every_rep": all((q.status, q.iterations, q.r0_final) ==
                                        (res[0].status, res[0].iterations, res[0].r0_final)
                                        for q in res),
@@ -300,7 +311,7 @@ def undersampling_sweep(ccs, dev, reps: int, peak: float, seed: int):
         if d == 7 and rho == 0.05:
             entry["paper_table3_s_k40"] = TABLE3_SECONDS[24]
         out.append(entry)
-        del csc, ptr, cols, y, ws, x_hat, r
+        del csc, ptr, cols, y, ws, x_hat, r, x_dev, x_out
         torch.cuda.empty_cache()
     return {"reps": reps, "l2": "flushed before every decode (512 MB write)", "points": out}
 
@@ -308,7 +319,8 @@ def undersampling_sweep(ccs, dev, reps: int, peak: float, seed: int):
 def alpha_sweep(ccs, dev, seed: int, reps: int = 3):
     """The same n = 2^20 problem decoded with every alpha in [2, d] under both
     scores: the l0 decrease of Eq. (15) and the match count of Alg. 8 (whose
-    alpha = floor(d/2) + 1 is Parallel-LDDSR, Sec. 4.3.2).  Per setting:
+    alpha = floor(d/2) + 1 is Parallel-LDDSR, Sec. 4.3.2), then the shifted
+    variant (Sec. 4.3.1) beside Alg. 2 at alpha = 2.  Per setting:
     decodes/s (CUDA events, L2 flushed before each), iterations, outcome."""
     import numpy as np
     import torch
@@ -348,6 +360,28 @@ def alpha_sweep(ccs, dev, seed: int, reps: int = 3):
                         "status": names.get(last.status, last.status),
                         "exact_recovery": bool(last.status == ccs.CONVERGED and
                                                np.array_equal(x_hat.cpu().numpy(), p.x))})
+    # the shifted variant (Sec. 4.3.1) at alpha = 2 beside Alg. 2
+    for shifted in (False, True):
+        prm = ccs.params(shifted=shifted)
+        res_dev = ccs.result_buffer(reps + 1, dev)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(reps)]
+        for t in range(reps + 1):
+            flush.zero_()
+            if t > 0:
+                evs[t - 1][0].record(stream)
+            ccs.ccs_decode_parallel_l0_async(p.n, p.m, p.d, csc, ptr, cols, y, x_hat, r, None,
+                                             prm, res_dev[t * ccs.RESULT_BYTES:], ws, stream)
+            if t > 0:
+                evs[t - 1][1].record(stream)
+        torch.cuda.synchronize()
+        last = ccs.results_from_device(res_dev, reps + 1)[-1]
+        ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        out.append({"score": "l0_decrease", "alpha": 2, "shifted": shifted,
+                    "decodes_per_s": 1000.0 / ms, "iterations": last.iterations,
+                    "status": names.get(last.status, last.status),
+                    "exact_recovery": bool(last.status == ccs.CONVERGED and
+                                           np.array_equal(x_hat.cpu().numpy(), p.x))})
     return {"workload": f"n={p.n}, m={p.m}, d={p.d}, k={p.k}, gauss-grid", "points": out}
 
 

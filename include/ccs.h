@@ -193,6 +193,31 @@ CCS_API int ccs_measure(int32_t n, int32_t m, int32_t d, const int64_t *csr_ptr,
                 const int32_t *csr_cols, const double *x, double *y,
                 ccs_stream_t stream);
 
+/* ---- column-scaled A for signals that are not dissociated (Sec. 4.3.3) -------
+ *
+ * When x has equal nonzero values (binary or integer signals), scaling each
+ * column of A by an i.i.d. continuous random number makes the measured
+ * values identifiable again.  Here A diag(s) has one scale s_j per column.
+ *
+ * ccs_column_scales writes s[0..n): s_j = 1 + k_j 2^-20 with k_j the top 20
+ *   bits of the first draw of column j's SplitMix64 stream from `seed` (the
+ *   same stream rule as ccs_make_expander), so s_j is uniform on [1, 2) on a
+ *   2^-20 grid and products with small integers stay exact.  Device output;
+ *   CCS_EINVAL when n < 1 or s is null.
+ * ccs_measure_scaled writes y = A diag(s) x: y_i = ordered sum over the
+ *   row's columns j (ascending) of the nonzero products s_j * x_j, each
+ *   rounded once, from +0.0.  Arguments and errors as ccs_measure.
+ * ccs_unscale writes x_j = z_j / s_j (correctly rounded): decoding y with
+ *   any ccs_decode_* entry point on the unscaled A recovers z = s . x, and
+ *   this returns x.  In-place use (x == z) is allowed.
+ * All three are stream-ordered on `stream` and allocate nothing.          */
+CCS_API int ccs_column_scales(int32_t n, uint64_t seed, double *s, ccs_stream_t stream);
+CCS_API int ccs_measure_scaled(int32_t n, int32_t m, int32_t d, const int64_t *csr_ptr,
+                               const int32_t *csr_cols, const double *s, const double *x,
+                               double *y, ccs_stream_t stream);
+CCS_API int ccs_unscale(int32_t n, const double *s, const double *z, double *x,
+                        ccs_stream_t stream);
+
 /*
  * ccs_decode_parallel_l0 -- Parallel-l0 (Alg. 2).
  *

@@ -116,6 +116,9 @@ def lib() -> ctypes.CDLL:
         l.ccs_batch_workspace_size.restype = sz
         l.ccs_make_expander.argtypes = [i32, i32, i32, u64, P, P, P, P, sz, P]
         l.ccs_measure.argtypes = [i32, i32, i32, P, P, P, P, P]
+        l.ccs_column_scales.argtypes = [i32, u64, P, P]
+        l.ccs_measure_scaled.argtypes = [i32, i32, i32, P, P, P, P, P, P]
+        l.ccs_unscale.argtypes = [i32, P, P, P, P]
         l.ccs_decode_parallel_l0.argtypes = [i32, i32, i32, P, P, P, P, P, P, P,
                                              ctypes.POINTER(Params), ctypes.POINTER(Result),
                                              P, sz, P]
@@ -376,6 +379,39 @@ def measure(csr_ptr, csr_cols, x, m: int, d: int, stream=None):
     y = torch.empty(m, dtype=torch.float64, device=x.device)
     ccs_measure(n, m, d, csr_ptr, csr_cols, x, y, stream)
     return y
+
+
+def column_scales(n: int, seed: int, device="cuda", stream=None):
+    """One i.i.d. scale per column on [1, 2), grid 2^-20 (Sec. 4.3.3)."""
+    import torch
+    s = torch.empty(n, dtype=torch.float64, device=device)
+    _check(lib().ccs_column_scales(n, ctypes.c_uint64(seed), _ptr(s), _stream(stream)),
+           "ccs_column_scales")
+    return s
+
+
+def measure_scaled(csr_ptr, csr_cols, scales, x, m: int, d: int, stream=None):
+    """y = A diag(scales) x."""
+    import torch
+    n = x.numel()
+    _need(csr_ptr, torch.int64, m + 1, "csr_ptr")
+    _need(csr_cols, torch.int32, n * d, "csr_cols")
+    _need(scales, torch.float64, n, "scales")
+    _need(x, torch.float64, n, "x")
+    y = torch.empty(m, dtype=torch.float64, device=x.device)
+    _check(lib().ccs_measure_scaled(n, m, d, _ptr(csr_ptr), _ptr(csr_cols), _ptr(scales),
+                                    _ptr(x), _ptr(y), _stream(stream)), "ccs_measure_scaled")
+    return y
+
+
+def unscale(scales, z, stream=None):
+    """x = z / scales, the signal from the decode z of a scaled measurement."""
+    import torch
+    _need(z, torch.float64, scales.numel(), "z")
+    x = torch.empty_like(z)
+    _check(lib().ccs_unscale(scales.numel(), _ptr(scales), _ptr(z), _ptr(x), _stream(stream)),
+           "ccs_unscale")
+    return x
 
 
 class DecodeOutput(dict):

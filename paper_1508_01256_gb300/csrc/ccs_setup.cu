@@ -230,6 +230,50 @@ __device__ __forceinline__ double warp_ordered_row_sum(const int64_t *ptr, const
     return s;
 }
 
+// Column scales for signals that are not dissociated (Sec. 4.3.3): one
+// i.i.d. scale per column, uniform on [1, 2) to a grid of 2^-20 -- 1 plus the
+// top 20 bits of the first draw of the column's SplitMix64 stream, times
+// 2^-20 (exact in binary64).
+__global__ void k_column_scales(int n, uint64_t seed, double *s) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+        uint64_t state = seed + (uint64_t)(j + 1) * 0xd1b54a32d192ed03ull;
+        const uint64_t k = splitmix64(state) >> 44;
+        s[j] = __dadd_rn(1.0, (double)k * 0x1p-20);
+    }
+}
+
+// y = A diag(s) x: the row's nonzero products s_j x_j (each rounded once),
+// added in ascending j from +0.0 by the whole warp.
+__global__ void k_measure_scaled(int m, const int64_t *ptr, const int32_t *cols,
+                                 const double *sc, const double *x, double *y) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += warps) {
+        double s = 0.0;
+        const int64_t b = ptr[i], e = ptr[i + 1];
+        for (int64_t p0 = b; p0 < e; p0 += 32) {
+            const int64_t p = p0 + lane;
+            const int c = (p < e) ? cols[p] : 0;
+            const double vj = (p < e) ? __dmul_rn(sc[c], x[c]) : 0.0;
+            unsigned nz = __ballot_sync(0xffffffffu, vj != 0.0);
+            while (nz) {
+                const int src = __ffs(nz) - 1;
+                nz &= nz - 1;
+                s = __dadd_rn(s, __shfl_sync(0xffffffffu, vj, src));
+            }
+        }
+        if (lane == 0) y[i] = s;
+    }
+}
+
+// x_j = z_j / s_j (the decode of a column-scaled measurement is z = s . x).
+__global__ void k_unscale(int n, const double *sc, const double *z, double *x) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x)
+        x[j] = __ddiv_rn(z[j], sc[j]);
+}
+
 __global__ void k_measure(int m, const int64_t *ptr, const int32_t *cols, const double *x,
                           double *y) {
     const int lane = threadIdx.x & 31;
@@ -396,6 +440,45 @@ int ccs_measure(int32_t n, int32_t m, int32_t d, const int64_t *csr_ptr,
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const long long threads = (long long)m * 32;
     k_measure<<<grid_for(threads, 256), 256, 0, s>>>(m, csr_ptr, csr_cols, x, y);
+    CCS_CUDA_TRY(cudaGetLastError());
+    return CCS_OK;
+}
+
+int ccs_column_scales(int32_t n, uint64_t seed, double *scales, ccs_stream_t stream) {
+    if (n < 1 || !scales) {
+        set_last_error("ccs_column_scales: n < 1 or null output");
+        return CCS_EINVAL;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    k_column_scales<<<grid_for(n, 256), 256, 0, s>>>(n, seed, scales);
+    CCS_CUDA_TRY(cudaGetLastError());
+    return CCS_OK;
+}
+
+int ccs_measure_scaled(int32_t n, int32_t m, int32_t d, const int64_t *csr_ptr,
+                       const int32_t *csr_cols, const double *scales, const double *x,
+                       double *y, ccs_stream_t stream) {
+    int rc = check_sizes(n, m, d);
+    if (rc) return rc;
+    if (!csr_ptr || !csr_cols || !scales || !x || !y) {
+        set_last_error("ccs_measure_scaled: null pointer argument");
+        return CCS_EINVAL;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const long long threads = (long long)m * 32;
+    k_measure_scaled<<<grid_for(threads, 256), 256, 0, s>>>(m, csr_ptr, csr_cols, scales, x, y);
+    CCS_CUDA_TRY(cudaGetLastError());
+    return CCS_OK;
+}
+
+int ccs_unscale(int32_t n, const double *scales, const double *z, double *x,
+                ccs_stream_t stream) {
+    if (n < 1 || !scales || !z || !x) {
+        set_last_error("ccs_unscale: n < 1 or null pointer argument");
+        return CCS_EINVAL;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    k_unscale<<<grid_for(n, 256), 256, 0, s>>>(n, scales, z, x);
     CCS_CUDA_TRY(cudaGetLastError());
     return CCS_OK;
 }

@@ -560,3 +560,35 @@ def test_shifted_rejected_on_host_loop(ccs):
     with pytest.raises(ccs.CcsError) as ei:
         ccs.decode_parallel_l0(csc, ptr, cols, y, engine=ccs.ENGINE_HOST_LOOP, shifted=True)
     assert ei.value.code == ccs.CCS_EINVAL
+
+
+@pytest.mark.parametrize("n,seed", [(1, 3), (1000, 7), (2 ** 20 + 13, 99)])
+def test_column_scales_bitwise(ccs, orc, n, seed):
+    s = ccs.column_scales(n, seed)
+    assert np.array_equal(s.cpu().numpy(), orc.column_scales(n, seed))
+
+
+@pytest.mark.parametrize("shape", [(4096, 410, 7, 41), (2 ** 20, 1049, 9, 52),
+                                   (100000, 10000, 16, 800)])
+def test_scaled_pipeline_matches_oracle(ccs, orc, shape):
+    """Sec. 4.3.3 with +/-1 signals (not dissociated): scales, y = A diag(s) x,
+    Parallel-l0 decode of z = s . x, and x = z / s, each bit-identical to the
+    oracle; the decode recovers x exactly."""
+    import torch
+    n, m, d, k = shape
+    p = inputs.make_problem(n, m, d, k, 77 + d, "pm1")
+    A = orc.make_expander(n, m, d, p.a_seed)
+    csc, ptr, cols = upload_matrix(orc, A, m)
+    s = ccs.column_scales(n, 4242)
+    s_ref = orc.column_scales(n, 4242)
+    assert np.array_equal(s.cpu().numpy(), s_ref)
+    y = ccs.measure_scaled(ptr, cols, s, torch.from_numpy(p.x).cuda(), m, d)
+    y_ref = orc.measure_scaled(A, m, s_ref, p.x)
+    assert np.array_equal(y.cpu().numpy(), y_ref)
+    g = ccs.decode_parallel_l0(csc, ptr, cols, y)
+    ref = orc.parallel_l0(A, m, y_ref)
+    assert_same_decode(g, ref)
+    x = ccs.unscale(s, g.x_hat)
+    assert np.array_equal(x.cpu().numpy(), orc.unscale(s_ref, ref["x_hat"]))
+    if n >= 4096:
+        assert g.status == ccs.CONVERGED and np.array_equal(x.cpu().numpy(), p.x)
