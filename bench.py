@@ -385,6 +385,23 @@ def alpha_sweep(ccs, dev, seed: int, reps: int = 3):
     return {"workload": f"n={p.n}, m={p.m}, d={p.d}, k={p.k}, gauss-grid", "points": out}
 
 
+def phase_sweep(ccs, dev, seed: int):
+    """Sec. 5.1's phase-transition protocol, reduced to run in seconds:
+    n = 2^16, d = 7, four deltas, 5 problems per point; then banded signals
+    (Sec. 5.6) at delta = 0.1.  rho* is the 50 % point of the logistic fit."""
+    from paper_1508_01256_gb300 import phase
+    t0 = time.perf_counter()
+    res = phase.phase_transition(ccs, n=2 ** 16, d=7, deltas=[0.02, 0.1, 0.3, 0.5],
+                                 per_point=5, seed=seed, device=dev)
+    bands = [dict(phase.sweep_delta(ccs, 2 ** 16, 7, 0.1, per_point=5, seed=seed + 7,
+                                    model="banded", band=b, device=dev), band=b)
+             for b in (0.5, 0.9)]
+    return {"protocol": "Sec. 5.1: rho from 0.01 in steps of 0.01 while a point recovers; "
+                        "logistic 50 % point; n=2^16, d=7, 5 problems per point",
+            "deltas": res, "banded_delta_0.1": bands,
+            "wall_s": time.perf_counter() - t0}
+
+
 def batched_vs_plain(ccs, dev, count: int, seed: int, reps: int = 3):
     """Decodes/s of `count` mixed problems (n log-uniform in [2^12, 2^20],
     delta, rho, d drawn from the batched workload's sets) in ONE persistent
@@ -729,6 +746,9 @@ def run_ccs(args):
     alphas = None
     if args.alpha_sweep > 0:
         alphas = alpha_sweep(ccs, dev, seed=1000 * rank + 31)
+    phases = None
+    if args.phase > 0:
+        phases = phase_sweep(ccs, dev, seed=1000 * rank + 51)
     sweep = None
     if args.undersampling > 0:
         sweep = undersampling_sweep(ccs, dev, args.undersampling, measured_peaks()[0],
@@ -761,6 +781,7 @@ def run_ccs(args):
                 "serving": serving,
                 "undersampling": sweep,
                 "alpha_sweep": alphas,
+                "phase_transition": phases,
                 "wall_s_timed_region": wall}
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -786,6 +807,8 @@ def main():
                     help="requests in the serving run (0: skip)")
     ap.add_argument("--alpha-sweep", type=int, default=1,
                     help="alpha in [2, d] under both scores at n = 2^20 (0: skip)")
+    ap.add_argument("--phase", type=int, default=1,
+                    help="reduced phase-transition sweep (0: skip)")
     ap.add_argument("--undersampling", type=int, default=3,
                     help="timed decodes per point of the n/m ~ 10^3 sweep (0: skip)")
     args = ap.parse_args()
