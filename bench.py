@@ -536,11 +536,21 @@ def serving_run(ccs, dev, count: int, seed: int, load: float = 0.7,
     exact = sum(int(i.result.status == ccs.CONVERGED and
                     bool((reqs[q][4].cpu().numpy() == probs[q].x).all()))
                 for q, i in enumerate(infos))
+    # requests that do not converge run to max_iter (100 iterations): they set
+    # the tail of the latency distribution, so the converged ones are also
+    # reported on their own
+    lat_conv = sorted(1000.0 * (i.done_s - i.submit_s) for i in infos
+                      if i.result.status == ccs.CONVERGED)
     return {"requests": count, "offered_rate_per_s": rate, "load": load,
             "peak_decodes_per_s": closed, "decodes_per_s": count / span,
             "p50_ms": lat_ms[len(lat_ms) // 2], "p99_ms": lat_ms[min(len(lat_ms) - 1,
                                                                   int(0.99 * len(lat_ms)))],
-            "max_ms": lat_ms[-1], "rounds": st["rounds"], "peak_inflight": st["peak_inflight"],
+            "max_ms": lat_ms[-1],
+            "converged_requests": len(lat_conv),
+            "p50_ms_converged": lat_conv[len(lat_conv) // 2] if lat_conv else None,
+            "p99_ms_converged": lat_conv[min(len(lat_conv) - 1, int(0.99 * len(lat_conv)))]
+            if lat_conv else None,
+            "rounds": st["rounds"], "peak_inflight": st["peak_inflight"],
             "peak_state_bytes": st["peak_bytes"], "pool_bytes": pool_bytes,
             "iters_per_round": iters_per_round, "same_results_sample": same,
             "exact_recovery": exact,
