@@ -6,13 +6,19 @@
 
 namespace ccs {
 
+// Iterations each launch group of a batch runs alone before the launch that
+// merges the groups' tails (most converging problems finish within it).
+constexpr int kGroupIters = 16;
+
 static size_t batch_ws(const ccs_problem *probs, int32_t count) {
     size_t total = 0;
     for (int32_t q = 0; q < count; ++q) {
         if (check_sizes(probs[q].n, probs[q].m, probs[q].d) != CCS_OK) return 0;
         total += decode_ws_layout(probs[q].n, probs[q].m, nullptr, nullptr);
     }
-    return engine_header_bytes(count) + total;
+    // launch header, then the header of the resume-mode launches that merge
+    // the groups' tails, then each problem's arrays
+    return engine_header_bytes(count) + engine_resume_header_bytes(count) + total;
 }
 
 // Time every launch shape the kernel instances offer for each launch group
@@ -111,7 +117,8 @@ static int decode_batch_impl(const ccs_problem *probs, int32_t count, const ccs_
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *hdr = static_cast<char *>(ws);
-    char *base = hdr + engine_header_bytes(count);
+    char *rhdr = hdr + engine_header_bytes(count);
+    char *base = rhdr + engine_resume_header_bytes(count);
     std::vector<ProblemDev> pds(count);
     for (int32_t q = 0; q < count; ++q) {
         const ccs_problem &pr = probs[q];
@@ -179,6 +186,14 @@ static int decode_batch_impl(const ccs_problem *probs, int32_t count, const ccs_
     if (capture) return engine_capture(sub.data(), sizes, groups, p, hdr, dev_out, capture);
     std::vector<ccs_result> part(count);
     if (tuned) return autotune_groups(sub, sizes, groups, p, hdr, s, tuned);
+    if (groups > 1) {
+        // each group alone for its first iterations, then one launch over the
+        // whole batch for the problems still running, so that the groups'
+        // tails (problems that iterate to max_iter) overlap
+        for (int t = 0; t < count; ++t) sub[t].ctrl = header_ctrl(hdr, t);
+        return engine_run_phased(sub.data(), sizes, groups, count, p, kGroupIters, hdr, rhdr, s,
+                                 dev_out, out);
+    }
     for (int g = 0, first = 0; g < groups; first += sizes[g], ++g) {
         rc = engine_run(sub.data() + first, sizes[g], p, part.data() + first, hdr, s, dev_out);
         if (rc != CCS_OK) return rc;

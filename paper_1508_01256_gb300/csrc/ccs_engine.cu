@@ -465,8 +465,10 @@ size_t engine_resume_header_bytes(int P) {
     return resume_results_bytes(P) + stamps_bytes() + align_up(sizeof(ProblemDev) * (size_t)P, 256);
 }
 
-int engine_resume(ProblemDev *pds, int P, const ccs_params &prm, int iter_budget, ccs_result *out,
-                  char *hdr, cudaStream_t s) {
+// Enqueue one resume-mode launch (no host wait).  Results go to dev_out,
+// each at its problem's out_slot, or to the header's result area.
+static int engine_resume_launch(ProblemDev *pds, int P, const ccs_params &prm, int iter_budget,
+                                char *hdr, cudaStream_t s, ccs_result *dev_out) {
     LaunchPlan L;
     int rc = plan_launch(pds, P, prm, L);
     if (rc) return rc;
@@ -475,7 +477,7 @@ int engine_resume(ProblemDev *pds, int P, const ccs_params &prm, int iter_budget
     a.resume = 1;
     a.iter_budget = iter_budget > 0 ? iter_budget : 1;
     a.sync = reinterpret_cast<EngineSync *>(hdr);
-    a.dev_out = reinterpret_cast<ccs_result *>(hdr + sizeof(EngineSync));
+    a.dev_out = dev_out ? dev_out : reinterpret_cast<ccs_result *>(hdr + sizeof(EngineSync));
     ProblemDev *d_probs =
         reinterpret_cast<ProblemDev *>(hdr + resume_results_bytes(P) + stamps_bytes());
     a.probs = d_probs;
@@ -487,6 +489,48 @@ int engine_resume(ProblemDev *pds, int P, const ccs_params &prm, int iter_budget
                                              L.smem, s));
     prof_stop(ev, s);
     count_launches(1);
+    return CCS_OK;
+}
+
+// A batch whose launch classes (groups) would each end in their own long
+// tail of problems that iterate to max_iter: every group first runs alone,
+// freshly initialised, for at most group_iters iterations; then one launch
+// over every problem of the batch resumes the ones still running, so the
+// groups' tails share iterations.  pds: the groups' descriptors back to back
+// (their out_slot the caller's index, their control blocks distinct, in
+// `ctrl_hdr`, `count` of them); rhdr: engine_resume_header_bytes(count)
+// bytes.  Results: dev_out (each at out_slot), or host_out[out_slot].
+int engine_run_phased(ProblemDev *pds, const int *sizes, int groups, int count,
+                      const ccs_params &prm, int group_iters, char *ctrl_hdr, char *rhdr,
+                      cudaStream_t s, ccs_result *dev_out, ccs_result *host_out) {
+    CCS_CUDA_TRY(cudaMemsetAsync(ctrl_hdr, 0, sync_bytes(count), s));
+    for (int t = 0; t < count; ++t) pds[t].flags |= kPdFresh;
+    for (int g = 0, first = 0; g < groups; first += sizes[g], ++g) {
+        int rc = engine_resume_launch(pds + first, sizes[g], prm, group_iters, rhdr, s, nullptr);
+        if (rc) return rc;
+    }
+    for (int t = 0; t < count; ++t) pds[t].flags &= ~kPdFresh;
+    int rc = engine_resume_launch(pds, count, prm, 0x7fffffff, rhdr, s, dev_out);
+    if (rc || dev_out) return rc;
+    const size_t bytes = sizeof(EngineSync) + sizeof(ccs_result) * (size_t)count;
+    std::vector<char> h(bytes);
+    CCS_CUDA_TRY(cudaMemcpyAsync(h.data(), rhdr, bytes, cudaMemcpyDeviceToHost, s));
+    CCS_CUDA_TRY(cudaStreamSynchronize(s));
+    EngineSync hs;
+    std::memcpy(&hs, h.data(), sizeof(hs));
+    std::memcpy(host_out, h.data() + sizeof(EngineSync), sizeof(ccs_result) * (size_t)count);
+    if (hs.error) {
+        for (int t = 0; t < count; ++t) host_out[t].error = CCS_ETIMEOUT;
+        set_last_error("a bounded device wait exceeded the watchdog");
+        return CCS_ETIMEOUT;
+    }
+    return CCS_OK;
+}
+
+int engine_resume(ProblemDev *pds, int P, const ccs_params &prm, int iter_budget, ccs_result *out,
+                  char *hdr, cudaStream_t s) {
+    int rc = engine_resume_launch(pds, P, prm, iter_budget, hdr, s, nullptr);
+    if (rc) return rc;
     const size_t bytes = sizeof(EngineSync) + sizeof(ccs_result) * (size_t)P;
     std::vector<char> h(bytes);
     CCS_CUDA_TRY(cudaMemcpyAsync(h.data(), hdr, bytes, cudaMemcpyDeviceToHost, s));
