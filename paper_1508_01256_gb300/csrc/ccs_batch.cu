@@ -183,7 +183,6 @@ static int decode_batch_impl(const ccs_problem *probs, int32_t count, const ccs_
             sub[t] = pds[order[t]];
             sub[t].ctrl = header_ctrl(hdr, u);
         }
-    if (capture) return engine_capture(sub.data(), sizes, groups, p, hdr, dev_out, capture);
     std::vector<ccs_result> part(count);
     if (tuned) return autotune_groups(sub, sizes, groups, p, hdr, s, tuned);
     if (groups > 1) {
@@ -191,9 +190,13 @@ static int decode_batch_impl(const ccs_problem *probs, int32_t count, const ccs_
         // whole batch for the problems still running, so that the groups'
         // tails (problems that iterate to max_iter) overlap
         for (int t = 0; t < count; ++t) sub[t].ctrl = header_ctrl(hdr, t);
+        if (capture)
+            return engine_capture_phased(sub.data(), sizes, groups, count, p, kGroupIters, hdr,
+                                         rhdr, dev_out, capture);
         return engine_run_phased(sub.data(), sizes, groups, count, p, kGroupIters, hdr, rhdr, s,
                                  dev_out, out);
     }
+    if (capture) return engine_capture(sub.data(), sizes, groups, p, hdr, dev_out, capture);
     for (int g = 0, first = 0; g < groups; first += sizes[g], ++g) {
         rc = engine_run(sub.data() + first, sizes[g], p, part.data() + first, hdr, s, dev_out);
         if (rc != CCS_OK) return rc;

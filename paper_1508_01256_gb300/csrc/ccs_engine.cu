@@ -527,6 +527,70 @@ int engine_run_phased(ProblemDev *pds, const int *sizes, int groups, int count,
     return CCS_OK;
 }
 
+// engine_run_phased captured in a CUDA graph: the control blocks' reset,
+// each group's capped launch and the final launch over the whole batch.
+// The descriptors are uploaded now, outside the capture: the groups' (fresh)
+// to the launch header's descriptor area, the final launch's to the resume
+// header's.  Results of the final launch go to dev_out.
+int engine_capture_phased(ProblemDev *pds, const int *sizes, int groups, int count,
+                          const ccs_params &prm, int group_iters, char *ctrl_hdr, char *rhdr,
+                          ccs_result *dev_out, cudaGraphExec_t *exec) {
+    std::vector<ProblemDev> fresh(pds, pds + count), resumed(pds, pds + count);
+    for (int t = 0; t < count; ++t) {
+        fresh[t].flags |= kPdFresh;
+        resumed[t].flags &= ~kPdFresh;
+    }
+    ProblemDev *d_fresh =
+        reinterpret_cast<ProblemDev *>(ctrl_hdr + sync_bytes(count) + stamps_bytes());
+    ProblemDev *d_resumed =
+        reinterpret_cast<ProblemDev *>(rhdr + resume_results_bytes(count) + stamps_bytes());
+    std::vector<EngineArgs> args(groups + 1);
+    std::vector<LaunchPlan> plans(groups + 1);
+    for (int g = 0, first = 0; g <= groups; ++g) {
+        const bool last = g == groups;
+        const int P = last ? count : sizes[g];
+        ProblemDev *host = last ? resumed.data() : fresh.data() + first;
+        int rc = plan_launch(host, P, prm, plans[g]);
+        if (rc) return rc;
+        EngineArgs &a = args[g];
+        fill_args(a, plans[g], P, prm);
+        a.resume = 1;
+        a.iter_budget = last ? 0x7fffffff : (group_iters > 0 ? group_iters : 1);
+        a.sync = reinterpret_cast<EngineSync *>(rhdr);
+        a.dev_out = last ? dev_out : reinterpret_cast<ccs_result *>(rhdr + sizeof(EngineSync));
+        a.stamps = nullptr;
+        a.probs = last ? d_resumed : d_fresh + first;
+        if (!last) first += sizes[g];
+    }
+    // upload with the flags plan_launch set
+    CCS_CUDA_TRY(cudaMemcpy(d_fresh, fresh.data(), sizeof(ProblemDev) * count,
+                            cudaMemcpyHostToDevice));
+    CCS_CUDA_TRY(cudaMemcpy(d_resumed, resumed.data(), sizeof(ProblemDev) * count,
+                            cudaMemcpyHostToDevice));
+    cudaStream_t cs;
+    CCS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e1 = cudaMemsetAsync(ctrl_hdr, 0, sync_bytes(count), cs);
+        for (int g = 0; g <= groups && e1 == cudaSuccess; ++g) {
+            const LaunchPlan &L = plans[g];
+            void *kargs[] = {&args[g]};
+            e1 = cudaMemsetAsync(rhdr, 0, sizeof(EngineSync), cs);
+            if (e1 == cudaSuccess)
+                e1 = cudaLaunchCooperativeKernel((const void *)L.fn, dim3(L.G), dim3(L.threads),
+                                                 kargs, L.smem, cs);
+        }
+        e = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = e1;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "capturing the phased batch");
+    return CCS_OK;
+}
+
 int engine_resume(ProblemDev *pds, int P, const ccs_params &prm, int iter_budget, ccs_result *out,
                   char *hdr, cudaStream_t s) {
     int rc = engine_resume_launch(pds, P, prm, iter_budget, hdr, s, nullptr);

@@ -195,10 +195,14 @@ int engine_capture(ProblemDev *pds, const int *sizes, int groups, const ccs_para
                    ccs_result *dev_out, cudaGraphExec_t *exec);
 int engine_resume(ProblemDev *pds, int P, const ccs_params &prm, int iter_budget, ccs_result *out,
                   char *hdr, cudaStream_t s);
-// A multi-group batch with merged tails (see ccs_engine.cu).
+// A multi-group batch with merged tails (see ccs_engine.cu), run now or
+// captured in a CUDA graph.
 int engine_run_phased(ProblemDev *pds, const int *sizes, int groups, int count,
                       const ccs_params &prm, int group_iters, char *ctrl_hdr, char *rhdr,
                       cudaStream_t s, ccs_result *dev_out, ccs_result *host_out);
+int engine_capture_phased(ProblemDev *pds, const int *sizes, int groups, int count,
+                          const ccs_params &prm, int group_iters, char *ctrl_hdr, char *rhdr,
+                          ccs_result *dev_out, cudaGraphExec_t *exec);
 int check_params(const ccs_params *p, int d);
 
 }  // namespace ccs

@@ -468,7 +468,7 @@ def test_batch_graph_replays(ccs, orc):
     decodes the new signals (each against the oracle)."""
     import torch
     probs = inputs.batch_problems(10, seed=123, log2n_hi=15.0)
-    assert {p.d > 8 for p in probs} == {True, False}  # a graph of two launches
+    assert {p.d > 8 for p in probs} == {True, False}  # two groups and the merged tail
     items = [device_problem(ccs, p) for p in probs]
     outs, pbs = [], []
     for (csc, ptr, cols, y), p in zip(items, probs):
