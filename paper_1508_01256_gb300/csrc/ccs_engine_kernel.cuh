@@ -94,6 +94,10 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     return v;
 }
 
+__device__ __forceinline__ void red_release_add(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -172,22 +176,22 @@ static __device__ bool grid_barrier(const EngineArgs &a, unsigned index, bool ar
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        if (arrive) {
-            __threadfence();
-            atomicAdd(&a.sync->arrive, 1u);
-        }
+        // the CTA barrier above orders every thread's writes before thread 0's
+        // release; the acquire polls order the other CTAs' writes before what
+        // follows the CTA barrier below
+        if (arrive) red_release_add(&a.sync->arrive, 1u);
         const unsigned target = (index + 1u) * gridDim.x;
         const unsigned long long t0 = globaltimer();
-        while (ld_acquire(&a.sync->arrive) < target) {
-            if (*reinterpret_cast<volatile int *>(&a.sync->error) != 0 ||
-                globaltimer() - t0 > (unsigned long long)a.watchdog_ns) {
+        for (unsigned polls = 0; ld_acquire(&a.sync->arrive) < target; ++polls) {
+            if ((polls & 15u) == 15u &&
+                (*reinterpret_cast<volatile int *>(&a.sync->error) != 0 ||
+                 globaltimer() - t0 > (unsigned long long)a.watchdog_ns)) {
                 atomicOr(&a.sync->error, kErrWatchdog);
                 ok = 0;
                 break;
             }
             __nanosleep(32);
         }
-        __threadfence();
         if (ok && a.stamps && blockIdx.x == 0 && index < 3u * kMaxStampIters + 1u)
             a.stamps[index] = globaltimer();
         s_ok = ok;
@@ -347,6 +351,59 @@ __device__ __forceinline__ void issue_chunk(const EngineArgs &a, const ProblemDe
     uint64_t *bar = &S.full[slot];
     mbar_expect_tx(bar, tma);
     if (tma) bulk_g2s(S.stage + (size_t)slot * a.stage_bytes, P.csc_rows + col0 * P.d, tma, bar);
+}
+
+// Copies a one-problem launch issues ahead of its score phase (thread 0's
+// record).  The CSC does not change between iterations and a CTA's segment
+// of a lone problem is the same in every iteration, so the first chunks of
+// the next score phase can enter the ring before the phase begins, as can
+// the fingerprints once the grid barrier after their last store has opened.
+struct Prefetch {
+    int chunks;  // chunks 0 .. chunks-1 of the next segment are in the ring
+    bool fp;     // the next fingerprint copy is in flight
+};
+
+// Issue the first chunks of a segment (up to the ring depth) ahead of its
+// score phase.  Thread 0 only; the ring's previous chunks are all consumed.
+__device__ __forceinline__ void prefetch_chunks(const EngineArgs &a, const ProblemDev &P, int lo,
+                                                int hi, int per, ScoreSmem &S, unsigned chunk_seq,
+                                                Prefetch &pf, bool &ok) {
+    const int nchunks = (hi - lo + per - 1) / per;
+    const int c1 = min(nchunks, a.stages);
+    for (int c = pf.chunks; c < c1; ++c) {
+        const unsigned seq = chunk_seq + c;
+        const int slot = seq % a.stages;
+        if (!mbar_wait(a, &S.empty[slot], ((seq / a.stages) & 1u) ^ 1u)) {
+            ok = false;
+            return;
+        }
+        issue_chunk(a, P, lo, hi, c, per, S, slot);
+        pf.chunks = c + 1;
+    }
+}
+
+// Issue the fingerprint copy of the next score phase.  Thread 0 only, after
+// the grid barrier that follows the fingerprints' last generic stores.
+__device__ __forceinline__ void prefetch_fp(const ProblemDev &P, ScoreSmem &S, Prefetch &pf) {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    const uint32_t total = (uint32_t)align_up((size_t)P.m * (fp16_for(P.m) ? 2 : 1), 16);
+    mbar_expect_tx(S.fp_bar, total);
+    for (uint32_t off = 0; off < total; off += kFpChunk)
+        bulk_g2s(S.fp + off, P.fp + off, min((uint32_t)kFpChunk, total - off), S.fp_bar);
+    pf.fp = true;
+}
+
+// Before the CTA leaves: wait (bounded) for the copies issued ahead, which
+// no score phase will consume.  Thread 0 only.
+__device__ __forceinline__ void drain_prefetch(const EngineArgs &a, ScoreSmem &S,
+                                               unsigned chunk_seq, unsigned fp_seq, Prefetch &pf) {
+    for (int c = 0; c < pf.chunks; ++c) {
+        const unsigned seq = chunk_seq + c;
+        if (!mbar_wait(a, &S.full[seq % a.stages], (seq / a.stages) & 1u)) break;
+    }
+    if (pf.fp) mbar_wait(a, S.fp_bar, fp_seq & 1u);
+    pf.chunks = 0;
+    pf.fp = false;
 }
 
 // Exact score and apply of one column inside the stream, from its rows in
@@ -625,7 +682,8 @@ template <int DMAX, int THREADS>
 __device__ __forceinline__ void score_segment(const EngineArgs &a, const ProblemDev &P,
                                               int seg_lo, int seg_hi, int g, int it, int rmode,
                                               ScoreSmem &S, unsigned &chunk_seq,
-                                              unsigned &fp_seq, bool &ok) {
+                                              unsigned &fp_seq, bool &ok,
+                                              Prefetch *pf = nullptr) {
     const bool exact = rmode == 0;
     const int spos = a.shifted ? it % P.d : -1;  // shifted variant: candidate row
     const Segment sg{0, seg_lo, seg_hi, 0};
@@ -664,7 +722,7 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
 
     if (warp == 0) {
         if (lane == 0 && ok) {
-            if (use_fp) {
+            if (use_fp && !(pf && pf->fp)) {
                 // the fingerprints were written by generic stores (residual
                 // phase, any SM) before the grid barrier; order them before
                 // this thread's bulk (async-proxy) reads
@@ -675,7 +733,7 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
                 for (uint32_t off = 0; off < total; off += kFpChunk)
                     bulk_g2s(S.fp + off, P.fp + off, min((uint32_t)kFpChunk, total - off), S.fp_bar);
             }
-            for (int c = 0; c < nchunks; ++c) {
+            for (int c = pf ? pf->chunks : 0; c < nchunks; ++c) {
                 const unsigned seq = chunk_seq + c;
                 const int slot = seq % a.stages;
                 if (!mbar_wait(a, &S.empty[slot], ((seq / a.stages) & 1u) ^ 1u)) {
@@ -705,6 +763,10 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
     }
     chunk_seq += nchunks;
     if (use_fp) ++fp_seq;
+    if (pf && threadIdx.x == 0) {
+        pf->chunks = 0;  // taken by this segment (thread 0 is its producer)
+        pf->fp = false;
+    }
     __syncthreads();  // stream done, queue complete
     if (a.stamps && blockIdx.x == 0 && threadIdx.x == 0 && g < kMaxStampIters)
         a.stamps[kSubBase + 3 * g + 1] = globaltimer();
@@ -953,6 +1015,36 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
         s_rmode[p] = (int8_t)(__ldcg(&problem(a, p).ctrl->ordered) ? 1 : 0);
     __syncthreads();
 
+    // a lone problem: this CTA's column tiles are the same in every
+    // iteration, so once the stop rule has let the problem run another
+    // iteration, the fingerprint copy and the first CSC chunks of that score
+    // phase are issued at once, ahead of the iteration's set-up (thread 0
+    // keeps the record in shared memory)
+    __shared__ Prefetch pf;
+    constexpr int kPer = (kWarps - 1) * ((THREADS == 512) ? 2 : 1);  // tiles per chunk
+    auto my_tiles = [&](int &t0, int &t1) {
+        const long long tiles = (a.single.n + kTile - 1) / kTile;
+        t0 = (int)(tiles * blockIdx.x / gridDim.x);
+        t1 = (int)(tiles * (blockIdx.x + 1) / gridDim.x);
+    };
+    auto issue_ahead = [&](int g_next) {
+        if (a.probs || threadIdx.x != 0 || g_next >= a.iter_budget || s_status[0] != kRunning)
+            return;
+        int t0, t1;
+        my_tiles(t0, t1);
+        if (t1 <= t0) return;
+        if (a.single.flags & kPdUseFp) prefetch_fp(a.single, S, pf);
+        prefetch_chunks(a, a.single, t0, t1, kPer, S, chunk_seq, pf, ok);
+    };
+    if (threadIdx.x == 0) {
+        pf.chunks = 0;
+        pf.fp = false;
+    }
+    auto leave = [&]() {
+        if (threadIdx.x == 0) drain_prefetch(a, S, chunk_seq, fp_seq, pf);
+        fail_out(a);
+    };
+
     // ---- init: x_hat <- 0, r <- y (Alg. 2, first line) --------------------
     if (!a.probs) {
         // one problem: grid-stride over its columns and rows
@@ -992,7 +1084,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
                         });
     }
     if (!grid_barrier(a, bar++)) {
-        fail_out(a);
+        leave();
         return;
     }
     for (int p = threadIdx.x; p < a.P; p += THREADS) {
@@ -1015,6 +1107,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
         }
     }
     __syncthreads();
+    issue_ahead(0);
 
     for (int g = 0; g < a.iter_budget; ++g) {
         int any = 0;
@@ -1042,12 +1135,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
 
         // ---- score + apply ------------------------------------------------
         if (!a.probs) {
-            const long long tiles = (a.single.n + kTile - 1) / kTile;
-            const int t0 = (int)(tiles * blockIdx.x / gridDim.x);
-            const int t1 = (int)(tiles * (blockIdx.x + 1) / gridDim.x);
+            int t0, t1;
+            my_tiles(t0, t1);
             if (t1 > t0)
                 score_segment<DMAX, THREADS>(a, a.single, t0, t1, g, s_base[0] + g, s_rmode[0], S,
-                                             chunk_seq, fp_seq, ok);
+                                             chunk_seq, fp_seq, ok, &pf);
         } else {
             build_partition<THREADS>(a, s_status, s_pref, kPartScore);
             for_my_segments(a, s_status, s_pref, kPartScore,
@@ -1069,7 +1161,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
         }
         const bool skip = (a.debug_flags & kFlagSkipArrive) && blockIdx.x == 0 && g == 0;
         if (!grid_barrier(a, bar++, !skip) || skip) {
-            fail_out(a);
+            leave();
             return;
         }
 
@@ -1134,7 +1226,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
                             });
         }
         if (!grid_barrier(a, bar++)) {
-            fail_out(a);
+            leave();
             return;
         }
 
@@ -1158,7 +1250,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
             if (blockIdx.x == 0 && st != kRunning) P.ctrl->status = st;
         }
         __syncthreads();
+        issue_ahead(g + 1);
     }
+    if (threadIdx.x == 0) drain_prefetch(a, S, chunk_seq, fp_seq, pf);
     // every problem has stopped: CTA 0 publishes the results on the device
     if (a.dev_out && blockIdx.x == 0) {
         for (int p = threadIdx.x; p < a.P; p += THREADS) {
