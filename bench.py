@@ -492,12 +492,35 @@ def batched_vs_plain(ccs, dev, count: int, seed: int, reps: int = 3):
                         "autotuned (1: 1024 threads, 2: 512, 3: 768 a CTA)"}
 
 
+def latency_summary(ccs, infos) -> dict:
+    """p50 / p99 / max latency (ms) of served requests, overall and over the
+    converged ones (requests that do not converge run to max_iter = 100
+    iterations and set the tail)."""
+    lat = sorted(1000.0 * (i.done_s - i.submit_s) for i in infos)
+    conv = sorted(1000.0 * (i.done_s - i.submit_s) for i in infos
+                  if i.result.status == ccs.CONVERGED)
+
+    def pct(v, f):
+        return v[min(len(v) - 1, int(f * len(v)))] if v else None
+    return {"p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "max_ms": lat[-1],
+            "converged_requests": len(conv), "p50_ms_converged": pct(conv, 0.5),
+            "p99_ms_converged": pct(conv, 0.99)}
+
+
+SERVE_LOADS = (0.5, 0.6, 0.7, 0.8, 0.9, 1.0)
+
+
 def serving_run(ccs, dev, count: int, seed: int, load: float = 0.7,
-                pool_bytes: int = 8 << 30, max_batch: int = 512, iters_per_round: int = 2):
-    """Serving workload: `count` requests, n log-uniform 2^12..2^22, delta,
-    rho as in the batched workload, d in {7, 9}.  First all of them at once
-    (the server's peak decodes/s), then Poisson arrivals at `load` x that
-    rate; latency = result ready - submission, from the library's clock."""
+                pool_bytes: int = 8 << 30, max_batch: int = 512, iters_per_round: int = 2,
+                sweep_requests: int = 0):
+    """Serving workload: `count` distinct requests, n log-uniform 2^12..2^22,
+    delta, rho as in the batched workload, d in {7, 9}.  First all of them at
+    once (the server's peak decodes/s), then Poisson arrivals at `load` x that
+    rate; latency = result ready - submission, from the library's clock.
+    With sweep_requests > 0, an open-loop load sweep follows: at each load in
+    SERVE_LOADS, sweep_requests Poisson arrivals cycle through the distinct
+    problems (request q decodes problem q mod count into its own output slot
+    of a ring), each on a fresh server."""
     import random
 
     import numpy as np
@@ -541,6 +564,8 @@ def serving_run(ccs, dev, count: int, seed: int, load: float = 0.7,
     # reported on their own
     lat_conv = sorted(1000.0 * (i.done_s - i.submit_s) for i in infos
                       if i.result.status == ccs.CONVERGED)
+    sweep = load_sweep(ccs, dev, reqs, [i.result for i in infos], closed, sweep_requests,
+                       seed, pool_bytes, max_batch, iters_per_round) if sweep_requests > 0 else None
     return {"requests": count, "offered_rate_per_s": rate, "load": load,
             "peak_decodes_per_s": closed, "decodes_per_s": count / span,
             "p50_ms": lat_ms[len(lat_ms) // 2], "p99_ms": lat_ms[min(len(lat_ms) - 1,
@@ -555,7 +580,52 @@ def serving_run(ccs, dev, count: int, seed: int, load: float = 0.7,
             "iters_per_round": iters_per_round, "same_results_sample": same,
             "exact_recovery": exact,
             "workload": "n log-uniform 2^12..2^22, m/n in {0.01,0.05,0.1,0.3}, "
-                        "k/m in {0.05,0.1,0.2}, d in {7,9}, Poisson arrivals"}
+                        "k/m in {0.05,0.1,0.2}, d in {7,9}, Poisson arrivals",
+            "load_sweep": sweep}
+
+
+def load_sweep(ccs, dev, reqs, base, peak: float, count: int, seed: int, pool_bytes: int,
+               max_batch: int, iters_per_round: int) -> dict:
+    """Open-loop Poisson load sweep over SERVE_LOADS x `peak` (the closed-loop
+    decodes/s of the same request mix).  Request q decodes distinct problem
+    q mod D into output slot q mod R (R a multiple of D, so a slot always
+    holds the same problem's shape); a slot is reused only after its earlier
+    request was collected.  Every served result (status, iterations, final
+    ||r||_0) is checked against the same problem's result in the distinct
+    run."""
+    import numpy as np
+    import torch
+
+    D = len(reqs)
+    R = D * max(1, min(4, -(-count // D)))
+    outs = [(torch.empty_like(reqs[s % D][4]), torch.empty_like(reqs[s % D][5]))
+            for s in range(R)]
+
+    def request_of(q):
+        csc, ptr, cols, y = reqs[q % D][:4]
+        return (csc, ptr, cols, y) + outs[q % R]
+
+    points = []
+    rng = np.random.default_rng(seed + 1)
+    for load in SERVE_LOADS:
+        rate = load * peak
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
+        with ccs.Server(pool_bytes, max_batch=max_batch, iters_per_round=iters_per_round) as srv:
+            infos, waited = ccs.serve_stream(srv, request_of, count, arrivals, R)
+            st = srv.stats()
+        span = max(i.done_s for i in infos) - min(i.submit_s for i in infos)
+        same = all((i.result.status, i.result.iterations, i.result.r0_final) ==
+                   (base[q % D].status, base[q % D].iterations, base[q % D].r0_final)
+                   for q, i in enumerate(infos))
+        points.append(dict({"load": load, "offered_rate_per_s": rate,
+                            "decodes_per_s": count / span}, **latency_summary(ccs, infos),
+                           peak_inflight=st["peak_inflight"], rounds=st["rounds"],
+                           peak_state_bytes=st["peak_bytes"], slot_waits=waited,
+                           same_results=same))
+    del outs
+    torch.cuda.empty_cache()
+    return {"requests_per_load": count, "distinct_problems": D, "output_slots": R,
+            "peak_decodes_per_s": peak, "points": points}
 
 
 def run_reference(args):
@@ -752,7 +822,8 @@ def run_ccs(args):
         batched = batched_vs_plain(ccs, dev, args.batch, seed=1000 * rank + 4242)
     serving = None
     if args.serve > 0:
-        serving = serving_run(ccs, dev, args.serve, seed=1000 * rank + 777)
+        serving = serving_run(ccs, dev, args.serve, seed=1000 * rank + 777,
+                              sweep_requests=args.serve_sweep)
     alphas = None
     if args.alpha_sweep > 0:
         alphas = alpha_sweep(ccs, dev, seed=1000 * rank + 31)
@@ -815,6 +886,8 @@ def main():
                     help="problems in the batched-vs-plain comparison (0: skip)")
     ap.add_argument("--serve", type=int, default=256,
                     help="requests in the serving run (0: skip)")
+    ap.add_argument("--serve-sweep", type=int, default=10000,
+                    help="requests per load point of the serving load sweep (0: skip)")
     ap.add_argument("--alpha-sweep", type=int, default=1,
                     help="alpha in [2, d] under both scores at n = 2^20 (0: skip)")
     ap.add_argument("--phase", type=int, default=1,

@@ -615,3 +615,55 @@ def serve_poisson(server: Server, requests, arrivals_s, timeout_ms: int = 120000
         tickets.append(server.submit(*req))
     th.join()
     return infos
+
+
+def serve_stream(server: Server, request_of, count: int, arrivals_s, ring: int,
+                 timeout_ms: int = 120000):
+    """Open-loop serving of `count` requests: request q, the tuple
+    `request_of(q)`, is submitted at arrivals_s[q] (seconds from now).
+    `request_of` may hand out output buffers from a ring of `ring` slots
+    (requests q and q + ring share one), so request q is submitted only once
+    request q - ring has been collected.  Returns (TicketInfo list in
+    submission order, number of submissions that waited for their slot)."""
+    import time
+    tickets, infos = [], [None] * count
+    state = {"collected": 0, "error": None}
+
+    def collect():
+        try:
+            i = 0
+            while i < count:
+                if i >= len(tickets):
+                    time.sleep(0.0001)
+                    continue
+                info = server.wait(tickets[i], timeout_ms)
+                if info is None:
+                    raise RuntimeError(f"request {i} not finished within {timeout_ms} ms")
+                infos[i] = info
+                i += 1
+                state["collected"] = i
+        except BaseException as e:  # re-raised on the submitting thread
+            state["error"] = e
+
+    th = threading.Thread(target=collect, daemon=True)
+    th.start()
+    waited = 0
+    t0 = time.perf_counter()
+    for q in range(count):
+        delay = t0 + arrivals_s[q] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        if q >= ring and state["collected"] <= q - ring:
+            waited += 1
+            limit = time.perf_counter() + timeout_ms / 1000.0
+            while state["collected"] <= q - ring and state["error"] is None:
+                if time.perf_counter() > limit:
+                    raise RuntimeError(f"slot of request {q} not free within {timeout_ms} ms")
+                time.sleep(0.00005)
+        if state["error"] is not None:
+            break
+        tickets.append(server.submit(*request_of(q)))
+    th.join()
+    if state["error"] is not None:
+        raise state["error"]
+    return infos, waited

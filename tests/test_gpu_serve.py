@@ -117,3 +117,32 @@ def test_poll_reports_busy_then_done(ccs):
         with pytest.raises(ccs.CcsError):
             srv.poll(999999)
     _check_same_as_alone(ccs, reqs, infos)
+
+
+def test_serve_stream_ring_results_equal_alone(ccs):
+    """Open-loop stream over a ring of output slots (the serving load sweep's
+    driver): 48 requests cycle through 6 distinct problems and 12 output
+    slots; each slot's final contents equal its problem decoded alone, and
+    every result's (status, iterations, final ||r||_0) does too."""
+    import torch
+    probs = inputs.batch_problems(6, seed=99, log2n_hi=16.0, ds=(7, 9))
+    reqs = _requests(ccs, probs)
+    D, R, count = len(reqs), 12, 48
+    outs = [(torch.full_like(reqs[s % D][4], float("nan")),
+             torch.full_like(reqs[s % D][5], float("nan"))) for s in range(R)]
+
+    def request_of(q):
+        return tuple(reqs[q % D][:4]) + outs[q % R]
+
+    arrivals = np.cumsum(np.random.default_rng(3).exponential(0.0002, size=count))
+    with ccs.Server(512 << 20, max_batch=8, iters_per_round=2) as srv:
+        infos, waited = ccs.serve_stream(srv, request_of, count, arrivals, R)
+    alone = [ccs.decode_parallel_l0(*reqs[p][:4]) for p in range(D)]
+    for q, info in enumerate(infos):
+        a = alone[q % D]
+        assert info.result.error == 0
+        assert (info.result.status, info.result.iterations, info.result.r0_final) == \
+            (a.status, a.iterations, a.r0_final)
+    for s in range(R):
+        a = alone[s % D]
+        assert torch.equal(outs[s][0], a.x_hat) and torch.equal(outs[s][1], a.r)
