@@ -65,7 +65,9 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            l = ctypes.CDLL(build())
+            # CCS_ORACLE_LIB names another build of ccs_oracle.c to load: the
+            # planted-mistake test runs the pins against broken copies
+            l = ctypes.CDLL(os.environ.get("CCS_ORACLE_LIB") or build())
             i32, i64, u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
             l.oracle_splitmix64_next.argtypes = [ctypes.POINTER(u64)]
             l.oracle_splitmix64_next.restype = u64

@@ -319,3 +319,17 @@ def test_scaled_columns_recover_pm1_signals(orc, q, k, seed):
     assert res["status"] == orc.CONVERGED
     assert np.array_equal(res["x_hat"], s * x)
     assert np.array_equal(orc.unscale(s, res["x_hat"]), x)
+
+
+def test_negative_zero_is_zero(orc):
+    """||.||_0 counts -0.0 as zero (IEEE -0.0 == 0.0): a measurement of
+    signed zeros is already solved by x_hat = 0, and a column whose rows hold
+    -0.0 sees no nonzero value to propose."""
+    assert orc.l0(np.array([-0.0, 0.0, 1.0, -2.0])) == 2
+    A = orc.make_expander(40, 12, 3, 5)
+    y = np.full(12, -0.0)
+    res = orc.parallel_l0(A, 12, y)
+    assert (res["status"], res["iterations"]) == (orc.CONVERGED, 0)
+    assert not np.any(res["x_hat"])
+    accepted, omega, score, count = orc.score_column(A[0], np.where(np.arange(12) < 6, -0.0, 0.0))
+    assert not accepted and (omega, score, count) == (0.0, -3, 0)

@@ -115,6 +115,14 @@ def test_row_sum_is_ascending_sequential(orc):
     assert y[0] == 0.0
     r = orc.residual(A, 1, np.array([5.0]), x)
     assert r[0] == 5.0
+    # two rows whose sums tell ascending from descending order apart:
+    # row 0 holds (1, 1e16, -1e16): ascending (1 + 1e16) - 1e16 = 0, while
+    # descending (-1e16 + 1e16) + 1 = 1; row 1 holds (1e16, -1e16, 1):
+    # ascending 1, descending (1 - 1e16) + 1e16 = 0
+    A2 = np.array([[0], [0], [0], [1], [1], [1]], dtype=np.int32)
+    x2 = np.array([1.0, 1e16, -1e16, 1e16, -1e16, 1.0])
+    assert orc.measure(A2, 2, x2).tolist() == [0.0, 1.0]
+    assert orc.residual(A2, 2, np.array([3.0, 3.0]), x2).tolist() == [3.0, 2.0]
     # skip zeros and start from +0.0: an all-zero row gives +0.0
     y0 = orc.measure(A, 1, np.array([0.0, -0.0, 0.0]))
     assert y0[0] == 0.0 and not np.signbit(y0[0])
