@@ -597,7 +597,7 @@ def load_sweep(ccs, dev, reqs, base, peak: float, count: int, seed: int, pool_by
     import torch
 
     D = len(reqs)
-    R = D * max(1, min(4, -(-count // D)))
+    R = D * max(1, min(8, -(-count // D)))
     outs = [(torch.empty_like(reqs[s % D][4]), torch.empty_like(reqs[s % D][5]))
             for s in range(R)]
 
