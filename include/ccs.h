@@ -266,10 +266,13 @@ CCS_API int ccs_decode_parallel_l0_async(int32_t n, int32_t m, int32_t d,
 
 /*
  * ccs_decode_batch -- Parallel-l0 on `count` independent problems of any
- * sizes in one persistent cooperative launch (the iteration loop runs on the
+ * sizes in persistent cooperative launches (the iteration loop runs on the
  * device; each problem stops on its own rule and drops out of later
- * phases).  Per problem, the results are bit-identical to
- * ccs_decode_parallel_l0 on that problem alone.
+ * phases).  Problems of one class (d <= 8 or d > 8; fingerprints of r in
+ * shared memory or not) share a launch; when a batch holds several classes,
+ * each class's launch runs a few iterations, then one launch over the whole
+ * batch continues the problems still running.  Per problem, the results are
+ * bit-identical to ccs_decode_parallel_l0 on that problem alone.
  *
  * probs: host array of `count` descriptors (device pointers inside);
  * out: host array of `count` results.  Blocks until every problem has
@@ -307,9 +310,10 @@ CCS_API void ccs_autotune_reset(void);
 
 /* ---- CUDA graph of a batched decode -----------------------------------------
  *
- * ccs_batch_graph_create captures one ccs_decode_batch_async launch of these
- * problems (the launch header reset and the persistent kernel) into a CUDA
- * graph; the problem descriptors are uploaded to the workspace once, now.
+ * ccs_batch_graph_create captures the launches ccs_decode_batch_async makes
+ * for these problems (the launch header resets and the persistent kernels)
+ * into a CUDA graph; the problem descriptors are uploaded to the workspace
+ * once, now.
  * Each ccs_graph_launch replays the whole decode of every problem on the
  * same device arrays and workspace (write new y values in place between
  * replays to decode new measurements), results to DEVICE memory out_dev as
