@@ -219,8 +219,12 @@ extern "C" int ccs_server_create(const ccs_server_config *cfg, ccs_stream_t stre
         set_last_error("ccs_server_create: bad configuration");
         return CCS_EINVAL;
     }
+    if (reinterpret_cast<uintptr_t>(cfg->pool) & 255u) {
+        set_last_error("ccs_server_create: the pool must start on a 256-byte boundary");
+        return CCS_EINVAL;
+    }
     const size_t hdr = align_up(engine_resume_header_bytes(cfg->max_batch), 256);
-    if (cfg->pool_bytes <= hdr) {
+    if (cfg->pool_bytes < hdr + 256) {
         set_last_error("ccs_server_create: pool of %zu bytes cannot hold the %zu-byte launch header",
                        cfg->pool_bytes, hdr);
         return CCS_EBUDGET;
@@ -233,7 +237,9 @@ extern "C" int ccs_server_create(const ccs_server_config *cfg, ccs_stream_t stre
     }
     S->stream = reinterpret_cast<cudaStream_t>(stream);
     S->pool = static_cast<char *>(cfg->pool);
-    S->header_off = cfg->pool_bytes - hdr;  // launch header at the top of the pool
+    // launch header at the top of the pool, on a 256-byte boundary whatever
+    // pool_bytes is (its sync word and descriptors are accessed atomically)
+    S->header_off = (cfg->pool_bytes - hdr) & ~(size_t)255;
     S->alloc = new PoolAllocator(S->header_off);
     S->worker = std::thread(worker_loop, S);
     *out = S;

@@ -91,6 +91,15 @@ def test_bad_arguments_rejected_before_device_work(ccs):
     rc = l.ccs_decode_parallel_l0(100, 20, 7, None, 1, 1, 1, 1, 1, None, ctypes.byref(p),
                                   ctypes.byref(out), 1, 1 << 30, None)
     assert rc == ccs.CCS_EINVAL
+    # server configurations (checked before the device is touched): a pool
+    # off a 256-byte boundary, no batch slot, a pool too small for the header
+    h = ctypes.c_void_p()
+    for pool, nbytes, maxb, want in ((0x100008, 1 << 30, 8, ccs.CCS_EINVAL),
+                                     (0x100000, 1 << 30, 0, ccs.CCS_EINVAL),
+                                     (0x100000, 4096, 512, ccs.CCS_EBUDGET)):
+        cfg = ccs.ServerConfig(pool, nbytes, maxb, 2, ccs.params())
+        assert l.ccs_server_create(ctypes.byref(cfg), None, ctypes.byref(h)) == want, pool
+        assert not h.value
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
