@@ -28,6 +28,11 @@
  *    column order from +0.0, skipping zero entries; -0.0 counts as zero.
  *    Inputs must be finite.
  *  - Limits: 1 <= d <= 16, d <= m, n*d < 2^31.
+ *  - Alignment: csc_rows on 16 bytes (it is bulk-copied), binary64 and
+ *    int64 arrays on 8, csr_cols on 4, workspaces and the server pool on
+ *    256.  Fresh cudaMalloc / PyTorch allocations meet all of these; a
+ *    pointer that does not is refused with CCS_EINVAL before any device
+ *    work (on the device it would fault).
  */
 #ifndef CCS_H
 #define CCS_H

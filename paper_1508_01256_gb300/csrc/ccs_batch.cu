@@ -1,7 +1,9 @@
 // ccs_batch.cu -- many independent decodes in one persistent launch.
 #include <algorithm>
+#include <cstdio>
 #include <vector>
 
+#include "ccs_checks.cuh"
 #include "ccs_internal.cuh"
 
 namespace ccs {
@@ -114,6 +116,15 @@ static int decode_batch_impl(const ccs_problem *probs, int32_t count, const ccs_
     if (ws_bytes < need) {
         set_last_error("ccs_decode_batch: workspace %zu < %zu bytes", ws_bytes, need);
         return CCS_ENOMEM;
+    }
+    if ((rc = check_aligned("ccs_decode_batch", "ws", ws, kWorkspaceAlign))) return rc;
+    for (int32_t q = 0; q < count; ++q) {
+        const ccs_problem &pr = probs[q];
+        char who[48];
+        std::snprintf(who, sizeof who, "ccs_decode_batch: problem %d", q);
+        if ((rc = check_problem_arrays(who, pr.csc_rows, pr.csr_ptr, pr.csr_cols, pr.y, pr.x_hat,
+                                       pr.r, pr.r0_hist)))
+            return rc;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *hdr = static_cast<char *>(ws);

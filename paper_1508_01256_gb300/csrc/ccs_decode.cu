@@ -16,6 +16,7 @@
 //           integers.
 // A one-thread kernel then applies the stop rule (||r||_0 == 0, nothing
 // accepted, or max_iter) and records ||r||_0.
+#include "ccs_checks.cuh"
 #include "ccs_device.cuh"
 
 namespace ccs {
@@ -253,6 +254,9 @@ static int decode_setup(int32_t n, int32_t m, int32_t d, const int32_t *csc_rows
         set_last_error("%s: workspace %zu < %zu bytes", who, ws_bytes, need);
         return CCS_ENOMEM;
     }
+    if ((rc = check_problem_arrays(who, csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist)) ||
+        (rc = check_aligned(who, "ws", ws, kWorkspaceAlign)))
+        return rc;
     P = ProblemDev{};
     P.n = n;
     P.m = m;

@@ -24,6 +24,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "ccs_checks.cuh"
 #include "ccs_internal.cuh"
 
 namespace ccs {
@@ -254,11 +255,13 @@ extern "C" int ccs_server_submit(ccs_server *S, const ccs_problem *req, int64_t 
     int rc = check_sizes(req->n, req->m, req->d);
     if (rc) return rc;
     if ((rc = check_params(&S->cfg.params, req->d))) return rc;
-    if (!req->csc_rows || !req->csr_ptr || !req->csr_cols || !req->y || !req->x_hat || !req->r ||
-        (reinterpret_cast<uintptr_t>(req->csc_rows) & 15u)) {
-        set_last_error("ccs_server_submit: null or misaligned array");
+    if (!req->csc_rows || !req->csr_ptr || !req->csr_cols || !req->y || !req->x_hat || !req->r) {
+        set_last_error("ccs_server_submit: null array");
         return CCS_EINVAL;
     }
+    if ((rc = check_problem_arrays("ccs_server_submit", req->csc_rows, req->csr_ptr,
+                                   req->csr_cols, req->y, req->x_hat, req->r, req->r0_hist)))
+        return rc;
     Request R;
     R.prob = *req;
     R.state_bytes = request_state_bytes(req->n, req->m);

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 
+#include "ccs_checks.cuh"
 #include "ccs_internal.cuh"
 
 namespace ccs {
@@ -315,6 +316,27 @@ int check_sizes(int32_t n, int32_t m, int32_t d) {
     return CCS_OK;
 }
 
+int check_aligned(const char *who, const char *what, const void *p, unsigned align) {
+    if (reinterpret_cast<uintptr_t>(p) % align) {
+        set_last_error("%s: %s is not on a %u-byte boundary", who, what, align);
+        return CCS_EINVAL;
+    }
+    return CCS_OK;
+}
+
+int check_problem_arrays(const char *who, const int32_t *csc_rows, const int64_t *csr_ptr,
+                         const int32_t *csr_cols, const double *y, const double *x_hat,
+                         const double *r, const int64_t *r0_hist) {
+    int rc;
+    if ((rc = check_aligned(who, "csc_rows", csc_rows, 16))) return rc;
+    if ((rc = check_aligned(who, "csr_ptr", csr_ptr, 8))) return rc;
+    if ((rc = check_aligned(who, "csr_cols", csr_cols, 4))) return rc;
+    if ((rc = check_aligned(who, "y", y, 8))) return rc;
+    if ((rc = check_aligned(who, "x_hat", x_hat, 8))) return rc;
+    if ((rc = check_aligned(who, "r", r, 8))) return rc;
+    return check_aligned(who, "r0_hist", r0_hist, 8);
+}
+
 static size_t make_expander_ws(int32_t n, int32_t m) {
     (void)n;
     const size_t nblocks = ((size_t)m + kScanBlock - 1) / kScanBlock;
@@ -383,6 +405,10 @@ int ccs_make_expander(int32_t n, int32_t m, int32_t d, uint64_t seed, int32_t *c
                        make_expander_ws(n, m));
         return CCS_ENOMEM;
     }
+    if ((rc = check_problem_arrays("ccs_make_expander", csc_rows, csr_ptr, csr_cols, nullptr,
+                                   nullptr, nullptr, nullptr)) ||
+        (rc = check_aligned("ccs_make_expander", "ws", ws, kWorkspaceAlign)))
+        return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *base = static_cast<char *>(ws);
     int32_t *deg = reinterpret_cast<int32_t *>(base);
@@ -437,6 +463,10 @@ int ccs_measure(int32_t n, int32_t m, int32_t d, const int64_t *csr_ptr,
         set_last_error("ccs_measure: null pointer argument");
         return CCS_EINVAL;
     }
+    if ((rc = check_problem_arrays("ccs_measure", nullptr, csr_ptr, csr_cols, y, nullptr,
+                                   nullptr, nullptr)) ||
+        (rc = check_aligned("ccs_measure", "x", x, 8)))
+        return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const long long threads = (long long)m * 32;
     k_measure<<<grid_for(threads, 256), 256, 0, s>>>(m, csr_ptr, csr_cols, x, y);
@@ -449,6 +479,7 @@ int ccs_column_scales(int32_t n, uint64_t seed, double *scales, ccs_stream_t str
         set_last_error("ccs_column_scales: n < 1 or null output");
         return CCS_EINVAL;
     }
+    if (int rc = check_aligned("ccs_column_scales", "s", scales, 8)) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     k_column_scales<<<grid_for(n, 256), 256, 0, s>>>(n, seed, scales);
     CCS_CUDA_TRY(cudaGetLastError());
@@ -464,6 +495,11 @@ int ccs_measure_scaled(int32_t n, int32_t m, int32_t d, const int64_t *csr_ptr,
         set_last_error("ccs_measure_scaled: null pointer argument");
         return CCS_EINVAL;
     }
+    if ((rc = check_problem_arrays("ccs_measure_scaled", nullptr, csr_ptr, csr_cols, y, nullptr,
+                                   nullptr, nullptr)) ||
+        (rc = check_aligned("ccs_measure_scaled", "x", x, 8)) ||
+        (rc = check_aligned("ccs_measure_scaled", "s", scales, 8)))
+        return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const long long threads = (long long)m * 32;
     k_measure_scaled<<<grid_for(threads, 256), 256, 0, s>>>(m, csr_ptr, csr_cols, scales, x, y);
@@ -477,6 +513,11 @@ int ccs_unscale(int32_t n, const double *scales, const double *z, double *x,
         set_last_error("ccs_unscale: n < 1 or null pointer argument");
         return CCS_EINVAL;
     }
+    int rc;
+    if ((rc = check_aligned("ccs_unscale", "s", scales, 8)) ||
+        (rc = check_aligned("ccs_unscale", "z", z, 8)) ||
+        (rc = check_aligned("ccs_unscale", "x", x, 8)))
+        return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     k_unscale<<<grid_for(n, 256), 256, 0, s>>>(n, scales, z, x);
     CCS_CUDA_TRY(cudaGetLastError());

@@ -102,6 +102,52 @@ def test_bad_arguments_rejected_before_device_work(ccs):
         assert not h.value
 
 
+def test_misaligned_arrays_rejected_before_device_work(ccs):
+    """Device pointers off their alignment (a bulk copy from csc_rows wants 16
+    bytes, binary64 and int64 arrays 8, csr_cols 4, workspaces 256) are
+    refused on the host with CCS_EINVAL, naming the array, before any device
+    work: on the device they would fault."""
+    l = ccs.lib()
+    A = 0x10000000  # aligned fake device addresses, 1 MiB apart
+    ptrs = dict(csc=A, ptr=A + (1 << 20), cols=A + (2 << 20), y=A + (3 << 20),
+                x_hat=A + (4 << 20), r=A + (5 << 20), hist=A + (6 << 20))
+    ws = A + (64 << 20)
+    p = ccs.params()
+    out = ccs.Result()
+
+    def decode(**bad):
+        q = dict(ptrs, **{k: v for k, v in bad.items() if k != "ws"})
+        return l.ccs_decode_parallel_l0(100, 20, 7, q["csc"], q["ptr"], q["cols"], q["y"],
+                                        q["x_hat"], q["r"], q["hist"], ctypes.byref(p),
+                                        ctypes.byref(out), bad.get("ws", ws), 1 << 30, None)
+
+    for bad, name in ((dict(csc=A + 8), b"csc_rows"), (dict(ptr=A + (1 << 20) + 4), b"csr_ptr"),
+                      (dict(cols=A + (2 << 20) + 2), b"csr_cols"), (dict(y=A + (3 << 20) + 4), b"y"),
+                      (dict(x_hat=A + (4 << 20) + 1), b"x_hat"), (dict(r=A + (5 << 20) + 4), b"r"),
+                      (dict(hist=A + (6 << 20) + 4), b"r0_hist"), (dict(ws=ws + 128), b"ws")):
+        assert decode(**bad) == ccs.CCS_EINVAL, bad
+        assert name + b" is not on a" in l.ccs_last_error(), bad
+    # a batch names the problem
+    good = ccs.Problem(100, 20, 7, 0, ptrs["csc"], ptrs["ptr"], ptrs["cols"], ptrs["y"],
+                       ptrs["x_hat"], ptrs["r"], None)
+    bad = ccs.Problem(100, 20, 7, 0, ptrs["csc"], ptrs["ptr"], ptrs["cols"], ptrs["y"],
+                      ptrs["x_hat"] + 4, ptrs["r"], None)
+    arr = (ccs.Problem * 2)(good, bad)
+    res = (ccs.Result * 2)()
+    rc = l.ccs_decode_batch(arr, 2, ctypes.byref(p), res, ws, 1 << 30, None)
+    assert rc == ccs.CCS_EINVAL and b"problem 1: x_hat" in l.ccs_last_error()
+    rc = l.ccs_decode_batch(arr, 1, ctypes.byref(p), res, ws + 64, 1 << 30, None)
+    assert rc == ccs.CCS_EINVAL and b"ws" in l.ccs_last_error()
+    # set-up calls
+    rc = l.ccs_measure(100, 20, 7, ptrs["ptr"], ptrs["cols"], ptrs["x_hat"] + 4, ptrs["y"], None)
+    assert rc == ccs.CCS_EINVAL and b"ccs_measure: x is not" in l.ccs_last_error()
+    rc = l.ccs_make_expander(100, 20, 7, 1, ptrs["csc"], ptrs["ptr"], ptrs["cols"], ws + 16,
+                             1 << 30, None)
+    assert rc == ccs.CCS_EINVAL and b"ws" in l.ccs_last_error()
+    rc = l.ccs_unscale(100, ptrs["y"], ptrs["r"] + 2, ptrs["x_hat"], None)
+    assert rc == ccs.CCS_EINVAL and b"ccs_unscale: z" in l.ccs_last_error()
+
+
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     from paper_1508_01256_gb300 import ccs
     monkeypatch.setattr(ccs, "LIB_PATH", str(tmp_path / "missing.so"))
