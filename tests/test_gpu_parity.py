@@ -41,6 +41,21 @@ def test_expander_bitwise(ccs, orc, n, m, d):
     assert np.array_equal(cols.cpu().numpy(), ocols)
 
 
+def test_expander_rejection_branch_bitwise(ccs, orc):
+    """Seeds whose column 0 first draws a value Lemire's bounded method must
+    reject (a branch random seeds never reach): the device generator takes
+    the same next draw as the oracle."""
+    import rejection_seeds
+    for _, seed in rejection_seeds.rejected_first_draws():
+        for n, d in ((1, 1), (3, 2), (40, 5)):
+            csc, ptr, cols = ccs.make_expander(n, rejection_seeds.M, d, seed)
+            A = orc.make_expander(n, rejection_seeds.M, d, seed)
+            assert np.array_equal(csc.cpu().numpy(), A)
+            optr, ocols = orc.transpose(A, rejection_seeds.M)
+            assert np.array_equal(ptr.cpu().numpy(), optr)
+            assert np.array_equal(cols.cpu().numpy(), ocols)
+
+
 def test_expander_full_extreme_size(ccs, orc):
     """n = 2^24, m = 16777, d = 9: rows of ~9000 columns sorted on chip."""
     n, m, d = 2 ** 24, 16777, 9

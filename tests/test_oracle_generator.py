@@ -13,6 +13,8 @@ import pytest
 
 from paper_1508_01256_gb300 import inputs
 
+import rejection_seeds
+
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
@@ -137,3 +139,25 @@ def test_values_models():
     assert set(np.unique(pm)) == {-1.0, 1.0}
     b = inputs.values(1000, 5, "banded", band=0.5)
     assert np.max(np.unique(b, return_counts=True)[1]) >= 500
+
+
+
+def test_bounded_draw_rejection_branch(orc):
+    """Lemire's bounded draw maps x to floor(x m / 2^64) but first rejects x
+    when the low word x m mod 2^64 is below (2^64 - m) mod m, which makes every
+    row exactly equally likely.  The branch fires with probability about
+    m / 2^64, so random tests never reach it: the seeds of rejection_seeds
+    make column 0 first draw such an x (m = 6).  The row must come from the
+    first draw that is not rejected."""
+    M64, m = rejection_seeds.M64, rejection_seeds.M
+    threshold = (M64 - m) % m
+    differs = []
+    for x0, seed in rejection_seeds.rejected_first_draws():
+        assert (x0 * m) % M64 < threshold
+        draws = orc.splitmix64((seed + rejection_seeds.COLUMN_STEP) % M64, 8)
+        assert draws[0] == x0
+        accepted = next(x for x in draws[1:] if (x * m) % M64 >= threshold)
+        row = (accepted * m) >> 64
+        assert orc.make_expander(1, m, 1, seed)[0, 0] == row
+        differs.append(row != (x0 * m) >> 64)
+    assert any(differs)  # the rejected draw would have given another row

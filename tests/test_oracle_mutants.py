@@ -63,7 +63,17 @@ MUTANTS = [
      "        if (it == max_iter) { status = ORACLE_MAX_ITER; break; }\n        /* T"),
     ("||r||_0 counts -0.0 as nonzero",
      "if (r[i] != 0.0) ++c;", "if (r[i] != 0.0 || signbit(r[i])) ++c;"),
+    ("score pass: every column counted as accepted",
+     "        accepted += a;\n", "        accepted += 1;\n"),
+    ("history: r0 recorded at the old index",
+     "        it += 1;\n        if (r0_hist) r0_hist[it] = r0;\n    }\n    out->status = status;\n"
+     "    out->iterations = it;\n    out->r0_final = r0;\ndone:",
+     "        if (r0_hist) r0_hist[it] = r0;\n        it += 1;\n    }\n    out->status = status;\n"
+     "    out->iterations = it;\n    out->r0_final = r0;\ndone:"),
     # Serial-l0 (Alg. 1)
+    ("serial: shifted position counted from 1",
+     "oracle_score_column_shifted(d, rows, r, it % d, alpha,",
+     "oracle_score_column_shifted(d, rows, r, (it + 1) % d, alpha,"),
     ("serial: last row of N(j) not recomputed",
      "            for (int t = 0; t < d; ++t) {\n                int64_t i = rows[t];",
      "            for (int t = 0; t < d - 1; ++t) {\n                int64_t i = rows[t];"),
@@ -76,6 +86,13 @@ MUTANTS = [
      "            if (!seen) col[got++] = row;", "            col[got++] = row; (void)seen;"),
     ("expander: rows left unsorted",
      "            while (b >= 0 && col[b] > v) { col[b + 1] = col[b]; --b; }", ""),
+    ("transpose: columns visited in descending order",
+     "    for (int64_t j = 0; j < n; ++j)\n        for (int t = 0; t < d; ++t) {\n"
+     "            int32_t i = csc_rows[j * d + t];",
+     "    for (int64_t j = n - 1; j >= 0; --j)\n        for (int t = 0; t < d; ++t) {\n"
+     "            int32_t i = csc_rows[j * d + t];"),
+    ("Lemire: rejection threshold dropped",
+     "        while (low < threshold) {", "        while (0 && low < threshold) {"),
     ("transpose: row pointers not accumulated",
      "    for (int64_t i = 0; i < m; ++i) csr_ptr[i + 1] += csr_ptr[i];\n", ""),
     ("SplitMix64: wrong increment",
