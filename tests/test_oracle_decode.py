@@ -210,6 +210,16 @@ def test_stalled_when_nothing_qualifies(orc):
     res = orc.parallel_l0(A, 5, y)
     assert res["status"] == orc.STALLED and res["iterations"] == 0
     assert np.array_equal(res["r"], y)
+    # Serial-l0 (Alg. 1) stops the same way: a sweep that accepts nothing
+    ser = orc.serial_l0(A, 5, y, max_iter=50)
+    assert ser["status"] == orc.STALLED and ser["iterations"] == 0
+    assert np.array_equal(ser["r"], y) and not np.any(ser["x_hat"])
+    # ... and after progress: column 0 explains rows 0-2 (value 1), the rest
+    # is not in the range of A, so the second sweep accepts nothing
+    y2 = np.array([1.0, 1.0, 1.0, 4.0, 5.0])
+    ser = orc.serial_l0(A, 5, y2, max_iter=50)
+    assert ser["status"] == orc.STALLED and ser["iterations"] == 1
+    assert ser["x_hat"].tolist() == [1.0, 0.0]
 
 
 def test_max_iter_zero(orc):

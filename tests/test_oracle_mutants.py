@@ -36,6 +36,14 @@ MUTANTS = [
      "    return *score > alpha;"),
     ("shifted score: candidate from the wrong row",
      "const double w = r[rows[pos]];", "const double w = r[rows[(pos + 1) % d]];"),
+    ("shifted score: a zero candidate is scored like any other",
+     "    if (w == 0.0) {\n        *omega = 0.0;", "    if (0) {\n        *omega = 0.0;"),
+    ("iteration cap checked one iteration late",
+     "        if (it == max_iter) { status = ORACLE_MAX_ITER; break; }\n        /* T",
+     "        if (it == max_iter + 1) { status = ORACLE_MAX_ITER; break; }\n        /* T"),
+    ("serial: no stall exit",
+     "        if (accepted == 0) { status = ORACLE_STALLED; break; }\n        it += 1;",
+     "        it += 1;"),
     ("shifted decode: position counted from 1",
      "shifted ? it % d : -1", "shifted ? (it + 1) % d : -1"),
     # Alg. 2's loop body and stopping rule
@@ -134,7 +142,9 @@ def _pins_fail(so):
     failed = [ln for ln in proc.stdout.splitlines() if ln.startswith("FAILED")]
     if not failed and "Timeout" in proc.stdout + proc.stderr:
         failed = ["timeout"]
-    # exit code 1: some test failed (2 and up: the run itself broke)
+    if proc.returncode < 0:  # the mutant crashed the child (an out-of-bounds write)
+        failed = failed or [f"crashed (signal {-proc.returncode})"]
+    # exit code 1 (some test failed) or a crash: caught; 2 to 5: the run broke
     return proc.returncode, (failed[0] if failed else proc.stdout[-1500:])
 
 
@@ -155,6 +165,6 @@ def test_every_planted_mistake_fails_a_pin(tmp_path):
     for n, (rc, what) in results.items():
         print(f"{n}: exit {rc}, {what}")
     survivors = [n for n, (rc, _) in results.items() if rc == 0]
-    broken = {n: out for n, (rc, out) in results.items() if rc not in (0, 1)}
+    broken = {n: out for n, (rc, out) in results.items() if rc > 1}
     assert not broken, broken
     assert not survivors, f"mistakes no pin catches: {survivors}"
