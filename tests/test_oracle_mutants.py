@@ -158,6 +158,7 @@ def test_mutant_texts_are_unique():
 def test_every_planted_mistake_fails_a_pin(tmp_path):
     if shutil.which("gcc") is None:
         pytest.skip("gcc not found")
+    pytest.importorskip("pytest_timeout")  # the child runs stop a hanging pin with it
     sos = {name: _build_mutant(str(tmp_path), name, old, new) for name, old, new in MUTANTS}
     workers = max(1, min(len(sos), os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
