@@ -141,7 +141,6 @@ def test_values_models():
     assert np.max(np.unique(b, return_counts=True)[1]) >= 500
 
 
-
 def test_bounded_draw_rejection_branch(orc):
     """Lemire's bounded draw maps x to floor(x m / 2^64) but first rejects x
     when the low word x m mod 2^64 is below (2^64 - m) mod m, which makes every
