@@ -190,13 +190,41 @@ def _stream(stream):
     return stream.cuda_stream
 
 
-def _need(t, dtype, numel, name):
+def _need(t, dtype, numel, name, at_least=False):
+    """t must be a contiguous CUDA tensor of `dtype` with `numel` elements
+    (or at least that many): the library takes its address as a device
+    pointer, so anything else would be read or written out of bounds."""
     import torch
     if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
         raise TypeError(f"{name} must be a CUDA tensor")
-    if t.dtype != dtype or not t.is_contiguous() or t.numel() != numel:
-        raise ValueError(f"{name}: need contiguous {dtype} with {numel} elements, "
-                         f"got {t.dtype} {tuple(t.shape)}")
+    short = t.numel() < numel if at_least else t.numel() != numel
+    if t.dtype != dtype or not t.is_contiguous() or short:
+        raise ValueError(f"{name}: need contiguous {dtype} with {'at least ' if at_least else ''}"
+                         f"{numel} elements, got {t.dtype} {tuple(t.shape)}")
+
+
+def _need_problem(csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist, max_iter, outputs=True):
+    """The arrays of one problem (shapes from csc_rows [n, d] and y [m]);
+    outputs=False skips x_hat, r and r0_hist (allocated by this module)."""
+    import torch
+    if not isinstance(csc_rows, torch.Tensor) or csc_rows.dim() != 2:
+        raise TypeError("csc_rows must be a CUDA tensor of shape [n, d]")
+    n, d = csc_rows.shape
+    if not isinstance(y, torch.Tensor):
+        raise TypeError("y must be a CUDA tensor")
+    m = y.numel()
+    _need(csc_rows, torch.int32, n * d, "csc_rows")
+    _need(csr_ptr, torch.int64, m + 1, "csr_ptr")
+    _need(csr_cols, torch.int32, n * d, "csr_cols")
+    _need(y, torch.float64, m, "y")
+    if not outputs:
+        return n, m, d
+    _need(x_hat, torch.float64, n, "x_hat")
+    _need(r, torch.float64, m, "r")
+    if r0_hist is not None:
+        _need(r0_hist, torch.int64, max_iter + 1 if max_iter is not None else 1, "r0_hist",
+              at_least=True)
+    return n, m, d
 
 
 def params(alpha=2, max_iter=100, score_mode=SCORE_L0_DECREASE, engine=ENGINE_AUTO,
@@ -425,21 +453,21 @@ def decode_parallel_l0(csc_rows, csr_ptr, csr_cols, y, alpha=2, max_iter=100,
     """Parallel-l0 (Alg. 2) on one problem; returns x_hat, r (device tensors),
     r0_hist (host list), status, iterations, r0_final."""
     import torch
-    n, d = csc_rows.shape
-    m = y.numel()
-    _need(csc_rows, torch.int32, n * d, "csc_rows")
-    _need(csr_ptr, torch.int64, m + 1, "csr_ptr")
-    _need(csr_cols, torch.int32, n * d, "csr_cols")
-    _need(y, torch.float64, m, "y")
-    dev = y.device
     if out is None:
-        x_hat = torch.empty(n, dtype=torch.float64, device=dev)
+        if not isinstance(y, torch.Tensor) or y.device.type != "cuda":
+            raise TypeError("y must be a CUDA tensor")
+        dev, m = y.device, y.numel()
+        x_hat = torch.empty(csc_rows.shape[0], dtype=torch.float64, device=dev)
         r = torch.empty(m, dtype=torch.float64, device=dev)
         hist = torch.full((max_iter + 1,), -1, dtype=torch.int64, device=dev) if history else None
     else:
         x_hat, r, hist = out
+    n, m, d = _need_problem(csc_rows, csr_ptr, csr_cols, y, x_hat, r, hist, max_iter,
+                            outputs=out is not None)
     if ws is None:
-        ws = workspace(ccs_workspace_size(OP_DECODE, n, m, d), dev)
+        ws = workspace(ccs_workspace_size(OP_DECODE, n, m, d), y.device)
+    elif not isinstance(ws, torch.Tensor) or ws.device.type != "cuda" or not ws.is_contiguous():
+        raise TypeError("ws must be a contiguous CUDA tensor")
     p = params(alpha, max_iter, score_mode, engine, watchdog_ms, debug_flags, schedule, shifted)
     res = ccs_decode_parallel_l0(n, m, d, csc_rows, csr_ptr, csr_cols, y, x_hat, r, hist, p,
                                  ws, stream)
@@ -448,9 +476,13 @@ def decode_parallel_l0(csc_rows, csr_ptr, csr_cols, y, alpha=2, max_iter=100,
                         iterations=res.iterations, r0_final=res.r0_final, error=res.error)
 
 
-def problem(csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist=None) -> Problem:
-    n, d = csc_rows.shape
-    return Problem(n, y.numel(), d, 0, _ptr(csc_rows), _ptr(csr_ptr), _ptr(csr_cols),
+def problem(csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist=None,
+            max_iter: int | None = None) -> Problem:
+    """Descriptor of one problem for the batch, graph and server calls.
+    Every array is checked (CUDA, dtype, contiguous, size); r0_hist needs
+    max_iter + 1 entries when max_iter is given, else at least one."""
+    n, m, d = _need_problem(csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist, max_iter)
+    return Problem(n, m, d, 0, _ptr(csc_rows), _ptr(csr_ptr), _ptr(csr_cols),
                    _ptr(y), _ptr(x_hat), _ptr(r), _ptr(r0_hist))
 
 
@@ -469,7 +501,7 @@ def decode_batch(items, alpha=2, max_iter=100, score_mode=SCORE_L0_DECREASE,
         hist = torch.full((max_iter + 1,), -1, dtype=torch.int64, device=y.device) \
             if history else None
         outs.append((x_hat, r, hist))
-        probs.append(problem(csc, ptr, cols, y, x_hat, r, hist))
+        probs.append(problem(csc, ptr, cols, y, x_hat, r, hist, max_iter))
     if ws is None:
         ws = workspace(ccs_batch_workspace_size(probs), items[0][3].device)
     p = params(alpha, max_iter, score_mode, engine, debug_flags=debug_flags, shifted=shifted)
@@ -537,12 +569,13 @@ class Server:
                            params(alpha, max_iter, score_mode))
         self._h = ctypes.c_void_p()
         self._stream = torch.cuda.Stream(device=device) if stream is None else stream
+        self.max_iter = max_iter
         _check(lib().ccs_server_create(ctypes.byref(cfg), self._stream.cuda_stream,
                                        ctypes.byref(self._h)), "ccs_server_create")
         self._keep = {}
 
     def submit(self, csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist=None) -> int:
-        pb = problem(csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist)
+        pb = problem(csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist, self.max_iter)
         t = ctypes.c_int64()
         _check(lib().ccs_server_submit(self._h, ctypes.byref(pb), ctypes.byref(t)),
                "ccs_server_submit")

@@ -477,6 +477,30 @@ def test_async_watchdog_reports_on_device(ccs):
     assert ccs.results_from_device(res_dev, 1)[0].error == ccs.CCS_ETIMEOUT
 
 
+def test_binding_checks_arrays_before_the_library(ccs):
+    """Wrong dtypes, sizes, non-contiguous views and a history shorter than
+    max_iter + 1 are refused in Python, before any pointer reaches the
+    library."""
+    import torch
+    p = inputs.plain_small()
+    csc, ptr, cols, y = device_problem(ccs, p)
+    x_hat = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    r = torch.empty(p.m, dtype=torch.float64, device="cuda")
+    short = torch.empty(50, dtype=torch.int64, device="cuda")
+    with pytest.raises(ValueError, match="r0_hist"):
+        ccs.decode_parallel_l0(csc, ptr, cols, y, out=(x_hat, r, short))  # max_iter 100
+    with pytest.raises(ValueError, match="x_hat"):
+        ccs.problem(csc, ptr, cols, y, x_hat.float(), r)
+    with pytest.raises(ValueError, match="r"):
+        ccs.problem(csc, ptr, cols, y, x_hat, r[:-1])
+    with pytest.raises(ValueError, match="y"):
+        ccs.problem(csc, ptr, cols, torch.stack([y, y], 1)[:, 0], x_hat, r)  # strided view
+    with pytest.raises(TypeError, match="ws"):
+        ccs.decode_parallel_l0(csc, ptr, cols, y, ws=torch.empty(1 << 20, dtype=torch.uint8))
+    ccs.problem(csc, ptr, cols, y, x_hat, r, torch.empty(101, dtype=torch.int64, device="cuda"),
+                max_iter=100)  # long enough
+
+
 def test_batch_graph_replays(ccs, orc):
     """A batched decode captured in a CUDA graph: replays equal
     ccs_decode_batch, and writing new measurements y in place then replaying

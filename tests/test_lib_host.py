@@ -148,6 +148,29 @@ def test_misaligned_arrays_rejected_before_device_work(ccs):
     assert rc == ccs.CCS_EINVAL and b"ccs_unscale: z" in l.ccs_last_error()
 
 
+def test_binding_refuses_host_tensors():
+    """The binding hands tensors' addresses to the device as pointers, so a
+    host tensor is refused before any library call (on the device its
+    address would be an illegal access)."""
+    import torch
+    from paper_1508_01256_gb300 import ccs
+    n, m, d = 40, 12, 3
+    csc = torch.zeros((n, d), dtype=torch.int32)
+    ptr = torch.zeros(m + 1, dtype=torch.int64)
+    cols = torch.zeros(n * d, dtype=torch.int32)
+    y = torch.zeros(m, dtype=torch.float64)
+    x_hat = torch.zeros(n, dtype=torch.float64)
+    r = torch.zeros(m, dtype=torch.float64)
+    with pytest.raises(TypeError, match="csc_rows must be a CUDA tensor"):
+        ccs.problem(csc, ptr, cols, y, x_hat, r)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        ccs.decode_parallel_l0(csc, ptr, cols, y)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        ccs.decode_parallel_l0(csc, ptr, cols, y, out=(x_hat, r, None))
+    with pytest.raises(TypeError, match="csc_rows must be a CUDA tensor of shape"):
+        ccs.problem(cols, ptr, cols, y, x_hat, r)  # not [n, d]
+
+
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     from paper_1508_01256_gb300 import ccs
     monkeypatch.setattr(ccs, "LIB_PATH", str(tmp_path / "missing.so"))
