@@ -343,3 +343,24 @@ def test_negative_zero_is_zero(orc):
     assert not np.any(res["x_hat"])
     accepted, omega, score, count = orc.score_column(A[0], np.where(np.arange(12) < 6, -0.0, 0.0))
     assert not accepted and (omega, score, count) == (0.0, -3, 0)
+
+
+def test_repeated_update_accumulates(orc):
+    """Alg. 1 and Alg. 2 add omega to x_hat_j (x_hat_j <- x_hat_j + omega),
+    so a column accepted twice holds the sum of its updates.  Hand-worked
+    instance (count score, alpha = 2, d = 3), columns {0,1,2}, {0,3,4},
+    {1,5,6}, y = (1, 1, 5, 2, 2, 2, 2):
+      pass 1 accepts all three (omega 1, 2, 2): x_hat = (1, 2, 2),
+        r = (-2, -2, 4, 0, 0, 0, 0);
+      pass 2 accepts column 0 again with omega = -2: x_hat_0 = 1 - 2 = -1,
+        r = (0, 0, 6, 0, 0, 0, 0);
+      pass 3 accepts nothing: stalled after 2 iterations.
+    Serial-l0 reaches the same state sweep by sweep."""
+    A = np.array([[0, 1, 2], [0, 3, 4], [1, 5, 6]], dtype=np.int32)
+    y = np.array([1.0, 1.0, 5.0, 2.0, 2.0, 2.0, 2.0])
+    for decode in (orc.parallel_l0, orc.serial_l0):
+        res = decode(A, 7, y, alpha=2, score_mode=orc.SCORE_COUNT)
+        assert (res["status"], res["iterations"]) == (orc.STALLED, 2), decode.__name__
+        assert res["x_hat"].tolist() == [-1.0, 2.0, 2.0], decode.__name__
+        assert res["r"].tolist() == [0.0, 0.0, 6.0, 0.0, 0.0, 0.0, 0.0], decode.__name__
+        assert list(res["r0_hist"]) == [7, 3, 1], decode.__name__

@@ -105,7 +105,14 @@ MUTANTS = [
      "    for (int64_t i = 0; i < m; ++i) csr_ptr[i + 1] += csr_ptr[i];\n", ""),
     ("SplitMix64: wrong increment",
      "*state += 0x9e3779b97f4a7c15ULL;", "*state += 0x9e3779b97f4a7c14ULL;"),
+    ("unshifted decode scores only row 0",
+     "shifted ? it % d : -1", "shifted ? it % d : 0"),
+    ("serial: x_hat_j overwritten instead of accumulated",
+     "            x_hat[j] = x_hat[j] + omega;", "            x_hat[j] = omega;"),
     # column scaling (Sec. 4.3.3)
+    ("scales: 19 bits instead of 20",
+     "const uint64_t k = oracle_splitmix64_next(&state) >> 44;",
+     "const uint64_t k = oracle_splitmix64_next(&state) >> 45;"),
     ("scales: grid 2^-21",
      "s[j] = 1.0 + (double)k / 1048576.0;", "s[j] = 1.0 + (double)k / 2097152.0;"),
     ("scaled measure: scale dropped",
