@@ -283,6 +283,21 @@ def test_theorem_regime_on_gpu(ccs, orc, seed):
     assert np.array_equal(g.x_hat.cpu().numpy(), x)
 
 
+def test_repeated_update_accumulates_on_gpu(ccs, orc):
+    """The hand-worked instance of the oracle pin (count score, alpha = 2):
+    column 0 is accepted in two iterations and x_hat_0 = 1 + (-2) = -1,
+    bit-identical to the oracle."""
+    import torch
+    A = np.array([[0, 1, 2], [0, 3, 4], [1, 5, 6]], dtype=np.int32)
+    y = np.array([1.0, 1.0, 5.0, 2.0, 2.0, 2.0, 2.0])
+    csc, ptr, cols = upload_matrix(orc, A, 7)
+    g = ccs.decode_parallel_l0(csc, ptr, cols, torch.from_numpy(y).cuda(), alpha=2,
+                               score_mode=ccs.SCORE_COUNT)
+    ref = orc.parallel_l0(A, 7, y, alpha=2, score_mode=orc.SCORE_COUNT)
+    assert_same_decode(g, ref)
+    assert g.x_hat.cpu().numpy().tolist() == [-1.0, 2.0, 2.0]
+
+
 def test_workspace_reuse_and_dirty_outputs(ccs, orc):
     """A reused workspace and garbage in the output buffers change nothing."""
     import torch
