@@ -307,6 +307,21 @@ def test_measure_scaled_is_the_exact_sum(orc):
     assert np.array_equal(y * 2 ** 20, exact.astype(np.float64))
 
 
+def test_measure_scaled_order_and_rounding(orc):
+    """Each product s_j x_j is rounded once and the row adds them in
+    ascending column order from +0.0 (readings R6, R12).  With s = 1, the
+    rows (1, 1e16, -1e16) and (1e16, -1e16, 1) sum to (0, 1) in ascending
+    order, (1, 0) in descending order; with s_j = 1 + 2^-20 and x_j = 1 + 2^-33
+    the product 1 + 2^-20 + 2^-33 + 2^-53 rounds to 1 + 2^-20 + 2^-33 (ties
+    to even)."""
+    A = np.array([[0], [0], [0], [1], [1], [1]], dtype=np.int32)
+    x = np.array([1.0, 1e16, -1e16, 1e16, -1e16, 1.0])
+    assert orc.measure_scaled(A, 2, np.ones(6), x).tolist() == [0.0, 1.0]
+    s1, x1 = 1.0 + 2.0 ** -20, 1.0 + 2.0 ** -33
+    y = orc.measure_scaled(np.array([[0]], dtype=np.int32), 1, np.array([s1]), np.array([x1]))
+    assert y[0] == 1.0 + 2.0 ** -20 + 2.0 ** -33 and y[0] == s1 * x1
+
+
 @pytest.mark.parametrize("q,k,seed", [(5, 3, 0), (7, 3, 1), (7, 4, 2)])
 def test_scaled_columns_recover_pm1_signals(orc, q, k, seed):
     """Sec. 4.3.3: with every value of x equal to +1 (not dissociated: equal

@@ -115,6 +115,9 @@ MUTANTS = [
      "const uint64_t k = oracle_splitmix64_next(&state) >> 45;"),
     ("scales: grid 2^-21",
      "s[j] = 1.0 + (double)k / 1048576.0;", "s[j] = 1.0 + (double)k / 2097152.0;"),
+    ("scaled measure: rows summed in descending column order",
+     "        double acc = +0.0;\n        for (int64_t p = csr_ptr[i]; p < csr_ptr[i + 1]; ++p) {",
+     "        double acc = +0.0;\n        for (int64_t p = csr_ptr[i + 1] - 1; p >= csr_ptr[i]; --p) {"),
     ("scaled measure: scale dropped",
      "const double v = s[j] * x[j];", "const double v = x[j];"),
     ("unscale: multiplies",
