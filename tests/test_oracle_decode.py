@@ -379,3 +379,69 @@ def test_repeated_update_accumulates(orc):
         assert res["x_hat"].tolist() == [-1.0, 2.0, 2.0], decode.__name__
         assert res["r"].tolist() == [0.0, 0.0, 6.0, 0.0, 0.0, 0.0, 0.0], decode.__name__
         assert list(res["r0_hist"]) == [7, 3, 1], decode.__name__
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_shifted_candidate_position_every_iteration(orc, mode):
+    """Reading R11 at every iteration of a long shifted decode (100
+    iterations, so the position l mod d wraps around many times): with r the
+    residual before iteration l, column j is accepted exactly when the value
+    w = r at the (l mod d)-th of its ascending rows is nonzero and its score
+    reaches alpha, the score taken from its literal definition on the whole
+    vector (Eq. 15: ||r||_0 - ||r - w a_j||_0; the count score: the number of
+    rows of j holding w); the accepted omega is w."""
+    n, m, d = 1500, 150, 3
+    p = inputs.make_problem(n, m, d, inputs.round_half_up(0.2 * m), 1)
+    A = orc.make_expander(n, m, d, p.a_seed)
+    y = orc.measure(A, m, p.x)
+    res = orc.parallel_l0(A, m, y, alpha=2, score_mode=mode, shifted=True, trace=True)
+    assert res["iterations"] > 2 * d
+    dense = np.zeros((n, m))
+    dense[np.repeat(np.arange(n), d), A.ravel()] = 1.0
+    x_hat = np.zeros(n)
+    for it, idx, om in res["trace"]:
+        # r before this iteration: y - A x_hat by the residual rule (the count
+        # score oscillates to values that are no longer exact on the grid)
+        r = orc.residual(A, m, y, x_hat)
+        w = r[A[:, it % d]]
+        on_rows = r[A] == w[:, None]
+        if mode == 0:
+            after = r[None, :] - w[:, None] * dense
+            score = np.count_nonzero(r) - np.count_nonzero(after, axis=1)
+        else:
+            score = on_rows.sum(axis=1)
+        accept = (w != 0.0) & (score >= 2)
+        assert np.array_equal(np.nonzero(accept)[0], idx), it
+        assert np.array_equal(om, w[idx]), it
+        x_hat[idx] = x_hat[idx] + om
+    assert np.array_equal(x_hat, res["x_hat"])
+
+
+def test_serial_shifted_sweeps_replayed(orc):
+    """Reading R11 for Serial-l0 (Alg. 1) over 7 sweeps, so the position
+    t mod d wraps around twice.  The state before sweep t is the oracle's
+    result with max_iter = t.  The test replays sweep t by the definition:
+    columns in order, candidate w = r at the (t mod d)-th ascending row of
+    the column, accepted when w != 0 and the literal l0 decrease
+    ||r||_0 - ||r - w a_j||_0 reaches alpha, then x_hat_j += w and r = y -
+    A x_hat.  The replay must match the oracle with max_iter = t + 1."""
+    n, m, d = 1000, 100, 3
+    p = inputs.make_problem(n, m, d, inputs.round_half_up(0.2 * m), 2)
+    A = orc.make_expander(n, m, d, p.a_seed)
+    y = orc.measure(A, m, p.x)
+    full = orc.serial_l0(A, m, y, alpha=2, shifted=True, max_iter=40)
+    assert full["iterations"] > 2 * d
+    x_hat, r = np.zeros(n), y.copy()
+    for t in range(full["iterations"]):
+        pos = t % d
+        for j in range(n):
+            w = r[A[j, pos]]
+            if w == 0.0:
+                continue
+            after = r.copy()
+            after[A[j]] = after[A[j]] - w
+            if np.count_nonzero(r) - np.count_nonzero(after) >= 2:
+                x_hat[j] = x_hat[j] + w
+                r = orc.residual(A, m, y, x_hat)
+        nxt = orc.serial_l0(A, m, y, alpha=2, shifted=True, max_iter=t + 1)
+        assert np.array_equal(x_hat, nxt["x_hat"]) and np.array_equal(r, nxt["r"]), t

@@ -44,6 +44,10 @@ MUTANTS = [
     ("serial: no stall exit",
      "        if (accepted == 0) { status = ORACLE_STALLED; break; }\n        it += 1;",
      "        it += 1;"),
+    ("shifted decode: position does not wrap around d",
+     "shifted ? it % d : -1", "shifted ? (it < d ? it : d - 1) : -1"),
+    ("shifted score: rows counted from the end",
+     "const double w = r[rows[pos]];", "const double w = r[rows[d - 1 - pos]];"),
     ("shifted decode: position counted from 1",
      "shifted ? it % d : -1", "shifted ? (it + 1) % d : -1"),
     # Alg. 2's loop body and stopping rule
@@ -79,6 +83,9 @@ MUTANTS = [
      "        if (r0_hist) r0_hist[it] = r0;\n        it += 1;\n    }\n    out->status = status;\n"
      "    out->iterations = it;\n    out->r0_final = r0;\ndone:"),
     # Serial-l0 (Alg. 1)
+    ("serial: shifted position does not wrap around d",
+     "oracle_score_column_shifted(d, rows, r, it % d, alpha,",
+     "oracle_score_column_shifted(d, rows, r, it < d ? it : d - 1, alpha,"),
     ("serial: shifted position counted from 1",
      "oracle_score_column_shifted(d, rows, r, it % d, alpha,",
      "oracle_score_column_shifted(d, rows, r, (it + 1) % d, alpha,"),
