@@ -26,7 +26,13 @@
  *       the score is >= alpha (alpha an integer, 2 <= alpha <= d).
  *   R3  "while not converged": stop when ||r||_0 == 0 (converged), when an
  *       iteration accepts nothing (stalled: Parallel-l0 is deterministic,
- *       so nothing would change again) or after max_iter iterations.
+ *       so nothing would change again) or after max_iter iterations.  In
+ *       the shifted variant (Sec. 4.3.1) an iteration that accepts nothing
+ *       leaves r as it was but moves the candidate to the next position, so
+ *       it counts as an iteration, and the decode has stalled only when d
+ *       iterations in a row accepted nothing: every position has then been
+ *       tried on the same r, and the cycle would repeat.  The iteration that
+ *       completes such a run is not counted, as in the unshifted rule.
  *   R4  Sums: every row sum over A's columns runs in ascending column
  *       order, starts from +0.0 and skips zero entries (which leaves the
  *       result bit-identical); r_i = y_i - s_i is one subtraction.
@@ -362,14 +368,25 @@ int oracle_parallel_l0(int32_t n, int32_t m, int32_t d, const int32_t *csc_rows,
     int32_t it = 0;
     if (r0_hist) r0_hist[0] = r0;
     int32_t status;
+    /* R3: iterations in a row that accepted nothing; the decode stalls at 1
+     * (unshifted) or d (shifted: one try of every position on the same r) */
+    const int32_t stall_run = shifted ? d : 1;
+    int32_t empty_run = 0;
     for (;;) {
         if (r0 == 0) { status = ORACLE_CONVERGED; break; }
         if (it == max_iter) { status = ORACLE_MAX_ITER; break; }
         /* T <- {(j, omega_j) : ||r||_0 - ||r - omega_j a_j||_0 >= alpha} */
         int64_t accepted = oracle_score_all(n, d, csc_rows, r, alpha, score_mode,
                                             shifted ? it % d : -1, accept, omega, score);
-        if (accepted == 0) { status = ORACLE_STALLED; break; }
+        empty_run = (accepted == 0) ? empty_run + 1 : 0;
+        if (empty_run == stall_run) { status = ORACLE_STALLED; break; }
         if (trace) trace(trace_ctx, it, n, accept, omega);
+        if (accepted == 0) {
+            /* shifted: r is unchanged, the next iteration tries the next position */
+            it += 1;
+            if (r0_hist) r0_hist[it] = r0;
+            continue;
+        }
         /* for (j, omega_j) in T: x_hat_j <- x_hat_j + omega_j */
         for (int64_t j = 0; j < n; ++j)
             if (accept[j]) x_hat[j] = x_hat[j] + omega[j];
@@ -413,6 +430,10 @@ int oracle_serial_l0(int32_t n, int32_t m, int32_t d, const int32_t *csc_rows,
     int32_t it = 0;
     if (r0_hist) r0_hist[0] = r0;
     int32_t status;
+    /* R3, as in Parallel-l0: a sweep that accepts nothing stalls the
+     * unshifted decode; the shifted one stalls after d such sweeps in a row */
+    const int32_t stall_run = shifted ? d : 1;
+    int32_t empty_run = 0;
     for (;;) {
         if (r0 == 0) { status = ORACLE_CONVERGED; break; }
         if (it == max_iter) { status = ORACLE_MAX_ITER; break; }
@@ -436,7 +457,8 @@ int oracle_serial_l0(int32_t n, int32_t m, int32_t d, const int32_t *csc_rows,
             }
             ++accepted;
         }
-        if (accepted == 0) { status = ORACLE_STALLED; break; }
+        empty_run = (accepted == 0) ? empty_run + 1 : 0;
+        if (empty_run == stall_run) { status = ORACLE_STALLED; break; }
         it += 1;
         if (r0_hist) r0_hist[it] = r0;
     }

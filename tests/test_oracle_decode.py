@@ -445,3 +445,48 @@ def test_serial_shifted_sweeps_replayed(orc):
                 r = orc.residual(A, m, y, x_hat)
         nxt = orc.serial_l0(A, m, y, alpha=2, shifted=True, max_iter=t + 1)
         assert np.array_equal(x_hat, nxt["x_hat"]) and np.array_equal(r, nxt["r"]), t
+
+
+@pytest.mark.parametrize("serial", [False, True])
+def test_shifted_empty_iteration_moves_on(orc, serial):
+    """Reading R3 for the shifted variant (Sec. 4.3.1): an iteration whose
+    position accepts nothing leaves r unchanged but the next iteration tries
+    the next position, so it is counted and the decode goes on.  Columns
+    {0,1,2} and {0,3,4} hold x = (1, 2): y = (3, 1, 1, 2, 2).  At position 0
+    both candidates are r_0 = 3, which occurs once (score 1 < 2); at
+    position 1 the candidates are 1 and 2, which occur on two rows each, and
+    both are accepted.  Worked by hand: two iterations, converged, x_hat = x,
+    ||r||_0 history (5, 5, 0)."""
+    A = np.array([[0, 1, 2], [0, 3, 4]], dtype=np.int32)
+    y = np.array([3.0, 1.0, 1.0, 2.0, 2.0])
+    decode = orc.serial_l0 if serial else orc.parallel_l0
+    res = decode(A, 5, y, alpha=2, shifted=True)
+    assert (res["status"], res["iterations"]) == (orc.CONVERGED, 2)
+    assert res["x_hat"].tolist() == [1.0, 2.0]
+    assert res["r"].tolist() == [0.0] * 5
+    assert list(res["r0_hist"]) == [5, 5, 0]
+    # the unshifted decode takes the mode (1 on rows 1, 2; 2 on rows 3, 4)
+    # and needs no second position
+    plain = decode(A, 5, y, alpha=2)
+    assert (plain["status"], plain["iterations"]) == (orc.CONVERGED, 1)
+
+
+@pytest.mark.parametrize("serial", [False, True])
+def test_shifted_stalls_after_d_empty_iterations(orc, serial):
+    """One column {0,1,2} with r = (1, 2, 3): no value occurs twice, so no
+    position is ever accepted.  The shifted decode tries positions 0, 1, 2
+    on the same r and stalls when the third empty iteration completes the
+    run of d = 3; the first two are counted (history 3, 3, 3).  The
+    unshifted decode stalls at once, with no iteration counted."""
+    A = np.array([[0, 1, 2]], dtype=np.int32)
+    y = np.array([1.0, 2.0, 3.0])
+    decode = orc.serial_l0 if serial else orc.parallel_l0
+    res = decode(A, 3, y, alpha=2, shifted=True)
+    assert (res["status"], res["iterations"]) == (orc.STALLED, 2)
+    assert list(res["r0_hist"]) == [3, 3, 3]
+    assert res["x_hat"].tolist() == [0.0]
+    plain = decode(A, 3, y, alpha=2)
+    assert (plain["status"], plain["iterations"]) == (orc.STALLED, 0)
+    # with max_iter below the run the cap comes first
+    capped = decode(A, 3, y, alpha=2, shifted=True, max_iter=1)
+    assert (capped["status"], capped["iterations"]) == (orc.MAX_ITER, 1)

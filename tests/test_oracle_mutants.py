@@ -42,8 +42,17 @@ MUTANTS = [
      "        if (it == max_iter) { status = ORACLE_MAX_ITER; break; }\n        /* T",
      "        if (it == max_iter + 1) { status = ORACLE_MAX_ITER; break; }\n        /* T"),
     ("serial: no stall exit",
-     "        if (accepted == 0) { status = ORACLE_STALLED; break; }\n        it += 1;",
+     "        if (empty_run == stall_run) { status = ORACLE_STALLED; break; }\n        it += 1;",
      "        it += 1;"),
+    ("shifted decode: stalls after one empty iteration",
+     "position on the same r) */\n    const int32_t stall_run = shifted ? d : 1;",
+     "position on the same r) */\n    const int32_t stall_run = 1; (void)shifted;"),
+    ("shifted decode: an empty iteration does not move the position",
+     "            it += 1;\n            if (r0_hist) r0_hist[it] = r0;\n            continue;",
+     "            continue;"),
+    ("serial: shifted decode stalls after one empty sweep",
+     "such sweeps in a row */\n    const int32_t stall_run = shifted ? d : 1;",
+     "such sweeps in a row */\n    const int32_t stall_run = 1;"),
     ("shifted decode: position does not wrap around d",
      "shifted ? it % d : -1", "shifted ? (it < d ? it : d - 1) : -1"),
     ("shifted score: rows counted from the end",
@@ -62,17 +71,15 @@ MUTANTS = [
     ("row sum: gathers v[p] instead of v[col(p)]",
      "double vj = v[csr_cols[p]];", "double vj = v[p];"),
     ("no stall exit in Parallel-l0",
-     "        if (accepted == 0) { status = ORACLE_STALLED; break; }\n        if (trace)",
+     "        if (empty_run == stall_run) { status = ORACLE_STALLED; break; }\n        if (trace)",
      "        if (trace)"),
     ("init: r starts at 0",
      "    for (int64_t i = 0; i < m; ++i) r[i] = y[i];\n    int64_t r0 = oracle_l0(m, r);\n"
-     "    int32_t it = 0;\n    if (r0_hist) r0_hist[0] = r0;\n    int32_t status;\n    for (;;) {\n"
-     "        if (r0 == 0) { status = ORACLE_CONVERGED; break; }\n"
-     "        if (it == max_iter) { status = ORACLE_MAX_ITER; break; }\n        /* T",
+     "    int32_t it = 0;\n    if (r0_hist) r0_hist[0] = r0;\n    int32_t status;\n"
+     "    /* R3: iterations in a row",
      "    for (int64_t i = 0; i < m; ++i) r[i] = 0.0;\n    int64_t r0 = oracle_l0(m, r);\n"
-     "    int32_t it = 0;\n    if (r0_hist) r0_hist[0] = r0;\n    int32_t status;\n    for (;;) {\n"
-     "        if (r0 == 0) { status = ORACLE_CONVERGED; break; }\n"
-     "        if (it == max_iter) { status = ORACLE_MAX_ITER; break; }\n        /* T"),
+     "    int32_t it = 0;\n    if (r0_hist) r0_hist[0] = r0;\n    int32_t status;\n"
+     "    /* R3: iterations in a row"),
     ("||r||_0 counts -0.0 as nonzero",
      "if (r[i] != 0.0) ++c;", "if (r[i] != 0.0 || signbit(r[i])) ++c;"),
     ("score pass: every column counted as accepted",
