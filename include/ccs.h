@@ -409,7 +409,9 @@ CCS_API int ccs_server_destroy(ccs_server *s);
  * CCS_EINVAL; n = 2^20, m = 2^17, d = 7 fits.  The call allocates nothing:
  * no cudaMalloc, no cudaFree, no allocating library routine.  Its first call
  * on a device looks up that device's address of the array
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make that
+ * first call before any stream capture.  A cudaDeviceReset invalidates the
+ * kept address, so no call may follow a reset of the device.
  * Every call on a device shares the one array, which keeps the last call's
  * contents (the decode clears what must start at zero), so calls whose
  * work overlaps on the GPU race: issue them one after another on one stream

@@ -227,6 +227,24 @@ def _need_problem(csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist, max_iter, o
     return n, m, d
 
 
+def _need_abi_arrays(where, n, m, d, csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist,
+                     p: Params | None):
+    """The one-to-one decode calls take tensors or raw device addresses (ints,
+    passed through as the C ABI would take them).  Tensors are checked like
+    the conveniences' arrays, and against the sizes n, m, d given, so that a
+    short output never reaches the kernel."""
+    import torch
+    arrays = (csc_rows, csr_ptr, csr_cols, y, x_hat, r)
+    if not any(isinstance(a, torch.Tensor) for a in arrays + (r0_hist,)):
+        return
+    max_iter = p.max_iter if p is not None else 100
+    if isinstance(csc_rows, torch.Tensor) and csc_rows.dim() == 1:
+        csc_rows = csc_rows.view(-1, d) if csc_rows.numel() % max(d, 1) == 0 else csc_rows
+    got = _need_problem(csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist, max_iter)
+    if got != (n, m, d):
+        raise ValueError(f"{where}: arrays are for n, m, d = {got}, not {(n, m, d)}")
+
+
 def params(alpha=2, max_iter=100, score_mode=SCORE_L0_DECREASE, engine=ENGINE_AUTO,
            watchdog_ms=0, debug_flags=0, schedule=0, shifted=False) -> Params:
     p = Params()
@@ -263,6 +281,8 @@ def ccs_measure(n, m, d, csr_ptr, csr_cols, x, y, stream=None):
 
 def ccs_decode_parallel_l0(n, m, d, csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist,
                            p: Params | None, ws, stream=None) -> Result:
+    _need_abi_arrays("ccs_decode_parallel_l0", n, m, d, csc_rows, csr_ptr, csr_cols, y, x_hat,
+                     r, r0_hist, p)
     out = Result()
     rc = lib().ccs_decode_parallel_l0(
         n, m, d, _ptr(csc_rows), _ptr(csr_ptr), _ptr(csr_cols), _ptr(y), _ptr(x_hat), _ptr(r),
@@ -276,6 +296,8 @@ def ccs_decode_parallel_l0_async(n, m, d, csc_rows, csr_ptr, csr_cols, y, x_hat,
                                  p: Params | None, out_dev, ws, stream=None):
     """Enqueue a decode; its ccs_result lands in the device buffer out_dev
     (a tensor of >= RESULT_BYTES bytes, or a device address)."""
+    _need_abi_arrays("ccs_decode_parallel_l0_async", n, m, d, csc_rows, csr_ptr, csr_cols, y,
+                     x_hat, r, r0_hist, p)
     rc = lib().ccs_decode_parallel_l0_async(
         n, m, d, _ptr(csc_rows), _ptr(csr_ptr), _ptr(csr_cols), _ptr(y), _ptr(x_hat), _ptr(r),
         _ptr(r0_hist), ctypes.byref(p) if p is not None else None, _ptr(out_dev),
@@ -331,7 +353,11 @@ def results_from_device(buf, count: int) -> list[Result]:
 
 def ccs_decode_parallel_l0_noalloc(n, m, d, csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist,
                                    p: Params | None, stream=None) -> Result:
-    """The decode without a caller workspace (library-held static scratch)."""
+    """The decode without a caller workspace (library-held static scratch).
+    Tensors are checked like every other decode's arrays; ints are raw device
+    addresses, passed through unchecked as in C."""
+    _need_abi_arrays("ccs_decode_parallel_l0_noalloc", n, m, d, csc_rows, csr_ptr, csr_cols, y,
+                     x_hat, r, r0_hist, p)
     out = Result()
     rc = lib().ccs_decode_parallel_l0_noalloc(
         n, m, d, _ptr(csc_rows), _ptr(csr_ptr), _ptr(csr_cols), _ptr(y), _ptr(x_hat), _ptr(r),

@@ -1102,6 +1102,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
         if (blockIdx.x == 0) {
             P.ctrl->status = st;
             P.ctrl->iteration = 0;
+            P.ctrl->empty_run[0] = 0;
             P.ctrl->max_iter = a.max_iter;
             if (P.r0_hist) P.r0_hist[0] = r0;
         }
@@ -1231,11 +1232,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
         }
 
         // ---- stop rule ("while not converged", three ways to stop) ----------
+        // An iteration that accepts nothing stalls the decode; in the shifted
+        // variant it only moves the candidate to the next position, and the
+        // decode stalls when d iterations in a row accepted nothing (every
+        // position tried on the same r).  The run length lives in a two-slot
+        // ring by iteration parity: every CTA reads slot it & 1, CTA 0 writes
+        // slot (it + 1) & 1, so the phase has no read-write race.
         for (int p = threadIdx.x; p < a.P; p += THREADS) {
             if (s_status[p] != kRunning) continue;
             const ProblemDev &P = problem(a, p);
             int st;
-            if (__ldcg(&P.ctrl->acc[g & 3]) == 0) {
+            const int it_now = s_base[p] + g;
+            const bool empty = __ldcg(&P.ctrl->acc[g & 3]) == 0;
+            const int run = empty ? __ldcg(&P.ctrl->empty_run[it_now & 1]) + 1 : 0;
+            if (blockIdx.x == 0) P.ctrl->empty_run[(it_now + 1) & 1] = run;
+            if (empty && run >= (a.shifted ? P.d : 1)) {
                 st = CCS_STALLED;
             } else {
                 const long long r0 = __ldcg(&P.ctrl->r0);

@@ -44,7 +44,9 @@ struct alignas(64) DecodeCtrl {
     unsigned long long xmax[2]; // bits of an upper bound of every |x_hat_j| so far
                                 // at the start of iteration t (slot t & 1)
     int ordered;                // 1 once the problem runs the ordered residual
-    int pad[5];
+    int empty_run[2];           // iterations in a row that accepted nothing, before
+                                // iteration t (slot t & 1; persistent engine)
+    int pad[3];
 };
 static_assert(sizeof(DecodeCtrl) == 128, "DecodeCtrl layout");
 

@@ -12,7 +12,10 @@
 // Host code never uses the array's name as a device address (in host code it
 // names a host-side stand-in).  Instead, once per device and with that device
 // current, cudaGetSymbolAddress gives the real device address, which is
-// cached and passed to the kernel.
+// cached and passed to the kernel.  The cached address belongs to the
+// device's context as it was at that first call: after cudaDeviceReset the
+// module is loaded again and the address may change, so calls after a reset
+// are not supported.
 #include <mutex>
 
 #include "ccs_internal.cuh"

@@ -298,6 +298,37 @@ def test_repeated_update_accumulates_on_gpu(ccs, orc):
     assert g.x_hat.cpu().numpy().tolist() == [-1.0, 2.0, 2.0]
 
 
+@pytest.mark.parametrize("case", ["moves_on", "stalls"])
+def test_shifted_empty_iterations_on_gpu(ccs, orc, case):
+    """The hand-worked instances of the oracle pins on the shifted stall rule
+    (Sec. 4.3.1): an iteration that accepts nothing moves to the next
+    position and is counted; d of them in a row stall the decode.  Alone and
+    in a batch (where the run length persists across the launches that
+    merge the groups' tails), bit-identical to the oracle."""
+    import torch
+    if case == "moves_on":
+        A = np.array([[0, 1, 2], [0, 3, 4]], dtype=np.int32)
+        y = np.array([3.0, 1.0, 1.0, 2.0, 2.0])
+        want = (orc.CONVERGED, 2, [5, 5, 0])
+    else:
+        A = np.array([[0, 1, 2]], dtype=np.int32)
+        y = np.array([1.0, 2.0, 3.0])
+        want = (orc.STALLED, 2, [3, 3, 3])
+    m = y.size
+    csc, ptr, cols = upload_matrix(orc, A, m)
+    yd = torch.from_numpy(y).cuda()
+    ref = orc.parallel_l0(A, m, y, alpha=2, shifted=True)
+    assert (ref["status"], ref["iterations"], list(ref["r0_hist"])) == want
+    g = ccs.decode_parallel_l0(csc, ptr, cols, yd, alpha=2, shifted=True)
+    assert_same_decode(g, ref)
+    big = inputs.make_problem(20000, 2000, 3, 400, 77)
+    items = [(csc, ptr, cols, yd), device_problem(ccs, big)]
+    outs = ccs.decode_batch(items, history=True, shifted=True)
+    assert_same_decode(outs[0], ref)
+    A2, y2 = oracle_problem(orc, big)
+    assert_same_decode(outs[1], orc.parallel_l0(A2, big.m, y2, shifted=True))
+
+
 def test_workspace_reuse_and_dirty_outputs(ccs, orc):
     """A reused workspace and garbage in the output buffers change nothing."""
     import torch

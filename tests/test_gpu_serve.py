@@ -3,6 +3,7 @@
 Each served result must be bit-identical to the same request decoded alone,
 whatever else shares its rounds; admission must respect the memory pool; a
 request that can never fit is refused."""
+import ctypes
 import random
 import time
 
@@ -93,10 +94,27 @@ def test_refuses_request_that_cannot_fit(ccs):
         with pytest.raises(ccs.CcsError) as ei:
             srv.submit(csc, ptr, cols, y, x_hat, r)
         assert ei.value.code == ccs.CCS_EBUDGET
-        # a bad request is refused without disturbing the server
-        with pytest.raises(ccs.CcsError) as ei:
+        # a request without an output array is stopped by the binding before
+        # any pointer leaves it ...
+        with pytest.raises(TypeError):
             srv.submit(csc, ptr, cols, y, x_hat, None)
-        assert ei.value.code == ccs.CCS_EINVAL
+        # ... and, through the C ABI directly, refused by the library with
+        # CCS_EINVAL, without disturbing the server
+        small = inputs.make_problem(4096, 410, 7, 41, 10)
+        s_csc, s_ptr, s_cols, s_y = device_problem(ccs, small)
+        s_x = torch.empty(small.n, dtype=torch.float64, device="cuda")
+        s_r = torch.empty(small.m, dtype=torch.float64, device="cuda")
+        desc = ccs.problem(s_csc, s_ptr, s_cols, s_y, s_x, s_r)
+        desc.r = None  # null output pointer
+        ticket = ctypes.c_int64(-1)
+        rc = ccs.lib().ccs_server_submit(srv._h, ctypes.byref(desc), ctypes.byref(ticket))
+        assert rc == ccs.CCS_EINVAL and ticket.value == -1
+        assert srv.stats()["error"] == 0
+        # the server still decodes a good request afterwards
+        info = srv.wait(srv.submit(s_csc, s_ptr, s_cols, s_y, s_x, s_r))
+        alone = ccs.decode_parallel_l0(s_csc, s_ptr, s_cols, s_y)
+        assert info.result.error == 0 and info.result.status == alone.status
+        assert torch.equal(s_x, alone.x_hat) and torch.equal(s_r, alone.r)
 
 
 def test_poll_reports_busy_then_done(ccs):

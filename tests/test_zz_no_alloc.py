@@ -63,6 +63,45 @@ def test_noalloc_matches_workspace_entry_point_on_consecutive_calls(ccs):
             assert hist[:res.iterations + 1].cpu().tolist() == ref.r0_hist
 
 
+def test_noalloc_takes_no_device_memory(ccs):
+    """After a first call (which looks up the scratch's device address), more
+    calls leave the device's free memory exactly where it was: neither the
+    library nor the driver hands out memory for them."""
+    import torch
+    p = inputs.plain_at_scale(seed=5)
+    csc, ptr, cols, y = _device(ccs, p)
+    x_hat = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    r = torch.empty(p.m, dtype=torch.float64, device="cuda")
+    hist = torch.empty(101, dtype=torch.int64, device="cuda")
+    ccs.ccs_decode_parallel_l0_noalloc(p.n, p.m, p.d, csc, ptr, cols, y, x_hat, r, hist,
+                                       ccs.params())
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        ccs.ccs_decode_parallel_l0_noalloc(p.n, p.m, p.d, csc, ptr, cols, y, x_hat, r, hist,
+                                           ccs.params())
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before
+
+
+def test_noalloc_checks_tensor_arguments(ccs):
+    """Tensors handed to the binding are checked before a pointer reaches the
+    library: a short history or a wrong-sized output is refused on the host."""
+    import torch
+    p = inputs.plain_small(seed=6)
+    csc, ptr, cols, y = _device(ccs, p)
+    x_hat = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    r = torch.empty(p.m, dtype=torch.float64, device="cuda")
+    short_hist = torch.empty(10, dtype=torch.int64, device="cuda")
+    with pytest.raises(ValueError):
+        ccs.ccs_decode_parallel_l0_noalloc(p.n, p.m, p.d, csc, ptr, cols, y, x_hat, r,
+                                           short_hist, ccs.params(max_iter=100))
+    with pytest.raises(ValueError):
+        ccs.ccs_decode_parallel_l0_noalloc(p.n, p.m, p.d, csc, ptr, cols, y, x_hat[:-1], r,
+                                           None, ccs.params())
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(ccs):
     n, m, d = 2 ** 22, 2 ** 19, 7
     assert ccs.ccs_workspace_size(ccs.OP_DECODE, n, m, d) > ccs.ccs_noalloc_scratch_bytes()
