@@ -2,10 +2,12 @@
 """Benchmark: Parallel-l0 decodes per second on one GB300 (or N, as replicas).
 
 One step = one complete Parallel-l0 decode (Alg. 2: score all columns, apply,
-recompute r and ||r||_0, until the stop rule) of a fresh instance of the
-workload, inputs resident in HBM.  Default workload: n=2^20, m=2^17,
-k=round(0.2 m)=26214, d=7, N(0,1) nonzeros on the 2^-32 grid, uniform
-support and expander, one instance per call.
+recompute r and ||r||_0, until the stop rule) of an instance of the workload,
+inputs resident in HBM.  Default workload: extreme undersampling (Sec. 5.5
+shape, n/m ~ 10^3): n=2^24, m=16777, k=round(0.05 m)=839, d=9, N(0,1)
+nonzeros on the 2^-32 grid, uniform support and expander, one instance per
+call.  Its CSC alone (604 MB) is far larger than L2, so every iteration
+streams it from HBM.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...   # the CPU oracle on the host cores
@@ -50,12 +52,23 @@ def workload(name: str, seed: int):
 
 
 def workload_config(name: str, p) -> dict:
+    """The workload, identical on the GPU arm and the reference arm."""
     return {"workload": {"at-scale": "plain Parallel-l0 at scale",
                          "small": "plain Parallel-l0, single small instance",
-                         "extreme": "extreme undersampling n/m ~ 10^3",
+                         "extreme": "extreme undersampling n/m ~ 10^3 (rho=0.05, d=9)",
                          "table3": "Table 3 shape (delta=1e-3, rho=0.05, d=7)"}[name],
             "n": p.n, "m": p.m, "k": p.k, "d": p.d, "alpha": 2, "values": p.model,
-            "instances_per_step": 1}
+            "l2": "inputs larger than L2 (CSC alone 4dn bytes); L2 also flushed between "
+                  "steps (512 MB write)" if 4 * p.d * p.n > 2 ** 27 else
+                  "flushed between steps (512 MB write)"}
+
+
+def decode_bytes(p, iterations: int) -> int:
+    """Algorithmic bytes of one decode: per iteration 4dn (every column's d
+    row indices) + 8m (one read of r by the score) + 16m (y and r by the
+    residual); once, 8n (writing x_hat) and 16 k (the updates of the k
+    support columns, a lower bound of the accepted pairs)."""
+    return iterations * (4 * p.d * p.n + 24 * p.m) + 8 * p.n + 16 * p.k
 
 
 def vs_baseline(name: str, p, value: float):
@@ -189,13 +202,22 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 
 def oracle_instances(name: str, count: int, base_seed: int):
+    """`count` instances of the workload for the oracle, generated in
+    parallel host threads (the oracle's C routines release the GIL)."""
     import oracle
-    insts = []
-    for i in range(count):
+    insts = [None] * count
+
+    def gen(i):
         p = workload(name, base_seed + i)
         A = oracle.make_expander(p.n, p.m, p.d, p.a_seed)
         y = oracle.measure(A, p.m, p.x)
-        insts.append((p, A, y))
+        insts[i] = (p, A, y)
+
+    threads = [threading.Thread(target=gen, args=(i,)) for i in range(count)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
     return insts
 
 
@@ -229,10 +251,13 @@ def host_cores() -> int:
 
 
 def cpu_baseline(name: str, budget_s: float = 12.0):
+    """The oracle as it stands on the host cores: rounds of `cores` concurrent
+    single-threaded decodes of distinct instances of the workload, until
+    about `budget_s` of wall time (at least one round)."""
     cores = host_cores()
     insts = oracle_instances(name, cores, 777000)
     decodes, elapsed, rounds, exact = 0, 0.0, 0, True
-    while elapsed < budget_s and rounds < 8:
+    while rounds == 0 or (elapsed < budget_s and rounds < 8):
         dt, ok = oracle_round(insts)
         elapsed += dt
         decodes += len(insts)
@@ -267,7 +292,7 @@ def undersampling_sweep(ccs, dev, reps: int, peak: float, seed: int):
         p = inputs.extreme_undersampling(rho, d=d, seed=seed + i,
                                          model=model.replace("-scaled", ""))
         csc, ptr, cols = ccs.make_expander(p.n, p.m, p.d, p.a_seed, device=dev)
-        x_dev = torch.from_numpy(p.x).to(dev)
+        x_dev = p.x_device(dev)
         if scaled:
             # Sec. 4.3.3: A's columns scaled by i.i.d. numbers; the decode
             # recovers z = s . x and x = z / s
@@ -295,25 +320,80 @@ def undersampling_sweep(ccs, dev, reps: int, peak: float, seed: int):
         ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
         last = res[-1]
         it = last.iterations
-        alg = it * (4 * p.d * p.n + 8 * p.m)
+        alg = decode_bytes(p, it)
         gbs = alg / (ms * 1e-3) / 1e9
         x_out = ccs.unscale(sc, x_hat) if scaled else x_hat
         entry = {"n": p.n, "m": p.m, "d": p.d, "k": p.k, "rho": rho, "values": model,
                  "ms_per_decode": ms, "decodes_per_s": 1000.0 / ms, "iterations": it,
                  "status": names.get(last.status, last.status),
                  "exact_recovery": bool(last.status == ccs.CONVERGED and
-                                        np.array_equal(x_out.cpu().numpy(), p.x)),
+                                        torch.equal(x_out, x_dev)),
                  "same_every_rep": all((q.status, q.iterations, q.r0_final) ==
                                        (res[0].status, res[0].iterations, res[0].r0_final)
                                        for q in res),
                  "algorithmic_bytes": alg, "achieved_gbs": gbs, "frac": gbs / peak,
                  "column_updates_per_s": p.n * it / (ms * 1e-3)}
-        if d == 7 and rho == 0.05:
-            entry["paper_table3_s_k40"] = TABLE3_SECONDS[24]
         out.append(entry)
         del csc, ptr, cols, y, ws, x_hat, r, x_dev, x_out
         torch.cuda.empty_cache()
-    return {"reps": reps, "l2": "flushed before every decode (512 MB write)", "points": out}
+    return {"reps": reps, "l2": "flushed before every decode (512 MB write)",
+            "bytes": "per decode: iterations x (4 d n + 24 m) + 8 n + 16 k", "points": out}
+
+
+def table3_rows(ccs, dev, problems: int, peak: float, seed: int):
+    """Table 3's workload at its three sizes: n = 2^22, 2^24, 2^26, delta =
+    10^-3, rho = 0.05, d = 7, alpha = 2, `problems` distinct problems per
+    size, each decoded alone (CUDA events on the launching stream, L2
+    flushed before each).  Mean time of the converged decodes, as the
+    paper's table, beside its K40 times (context, not a target)."""
+    import torch
+
+    from paper_1508_01256_gb300 import inputs
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows = []
+    for log2n in (22, 24, 26):
+        n = 2 ** log2n
+        m = inputs.round_half_up(n * 1e-3)
+        k = inputs.round_half_up(0.05 * m)
+        x_hat = torch.empty(n, dtype=torch.float64, device=dev)
+        r = torch.empty(m, dtype=torch.float64, device=dev)
+        ws = ccs.workspace(ccs.ccs_workspace_size(ccs.OP_DECODE, n, m, 7), dev)
+        prm = ccs.params()
+        ms_ok, iters, conv, exact, alg = [], [], 0, 0, []
+        for t in range(problems):
+            p = inputs.make_problem(n, m, 7, k, seed + 100 * log2n + t)
+            csc, ptr, cols = ccs.make_expander(n, m, 7, p.a_seed, device=dev)
+            xd = p.x_device(dev)
+            y = ccs.measure(ptr, cols, xd, m, 7)
+            flush.zero_()
+            e0.record(stream)
+            res = ccs.ccs_decode_parallel_l0(n, m, 7, csc, ptr, cols, y, x_hat, r, None, prm,
+                                             ws, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            iters.append(res.iterations)
+            if res.status == ccs.CONVERGED:
+                conv += 1
+                ms = e0.elapsed_time(e1)
+                ms_ok.append(ms)
+                alg.append(decode_bytes(p, res.iterations) / (ms * 1e-3) / 1e9)
+                exact += bool(torch.equal(x_hat, xd))
+            del csc, ptr, cols, y, xd
+        del x_hat, r, ws
+        torch.cuda.empty_cache()
+        mean_ms = statistics.mean(ms_ok) if ms_ok else None
+        rows.append({"n": n, "m": m, "k": k, "d": 7, "problems": problems, "converged": conv,
+                     "exact_recovery": exact, "mean_ms_converged": mean_ms,
+                     "mean_iterations": statistics.mean(iters),
+                     "mean_achieved_gbs": statistics.mean(alg) if alg else None,
+                     "frac": statistics.mean(alg) / peak if alg else None,
+                     "paper_k40_s": TABLE3_SECONDS[log2n],
+                     "paper_over_this": (TABLE3_SECONDS[log2n] / (mean_ms * 1e-3))
+                     if mean_ms else None})
+    return {"workload": "Table 3: delta=1e-3, rho=0.05, d=7, alpha=2, gauss-grid",
+            "rows": rows}
 
 
 def alpha_sweep(ccs, dev, seed: int, reps: int = 3):
@@ -328,7 +408,7 @@ def alpha_sweep(ccs, dev, seed: int, reps: int = 3):
     from paper_1508_01256_gb300 import inputs
     p = inputs.plain_at_scale(seed=seed)
     csc, ptr, cols = ccs.make_expander(p.n, p.m, p.d, p.a_seed, device=dev)
-    y = ccs.measure(ptr, cols, torch.from_numpy(p.x).to(dev), p.m, p.d)
+    y = ccs.measure(ptr, cols, p.x_device(dev), p.m, p.d)
     ws = ccs.workspace(ccs.ccs_workspace_size(ccs.OP_DECODE, p.n, p.m, p.d), dev)
     x_hat = torch.empty(p.n, dtype=torch.float64, device=dev)
     r = torch.empty(p.m, dtype=torch.float64, device=dev)
@@ -650,14 +730,16 @@ def run_reference(args):
             "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": vs_baseline(args.workload, p, value),
             "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_config(args.workload, p), instances_per_step=cores),
+            "config": dict(workload_config(args.workload, p),
+                           parallelism=f"replicas{args.gpus}"),
             "e2e": {"value": value, "unit": "decodes/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "cpu_baseline": {"value": value, "unit": "decodes/s", "cores": cores,
                              "kind": "oracle",
                              "sample": f"each step: {cores} concurrent single-threaded oracle "
-                                       f"decodes, one per host thread"},
-            "exact_recovery": exact, "gpu_launches": 0}
+                                       f"decodes of distinct instances of the workload, one "
+                                       f"per host thread (instance generation untimed)"},
+            "decodes_per_step": cores, "exact_recovery": exact, "gpu_launches": 0}
     print(json.dumps(line), flush=True)
 
 
@@ -690,7 +772,7 @@ def run_ccs(args):
     for i in range(args.instances):
         p = workload(args.workload, 1000 * rank + 17 + i)
         csc, ptr, cols = ccs.make_expander(p.n, p.m, p.d, p.a_seed, device=dev)
-        y = ccs.measure(ptr, cols, torch.from_numpy(p.x).to(dev), p.m, p.d)
+        y = ccs.measure(ptr, cols, p.x_device(dev), p.m, p.d)
         insts.append((p, csc, ptr, cols, y))
     p0 = insts[0][0]
     ws = ccs.workspace(ccs.ccs_workspace_size(ccs.OP_DECODE, p0.n, p0.m, p0.d), dev)
@@ -788,9 +870,9 @@ def run_ccs(args):
     value = job_rate(decodes, world, total_s)
     e2e_value = job_rate(e2e_steps, world, e2e_t)
 
-    # roofline of the dominant kernel.  Algorithmic bytes of one iteration:
-    # 4 d n (every column's d row indices) + 8 m (one read of r); a decode
-    # launch moves that once per iteration.
+    # roofline of the dominant kernel, the persistent launch that runs a
+    # whole decode: its algorithmic bytes are decode_bytes() of the mean
+    # iteration count.  The score phase alone moves 4 d n + 8 m per iteration.
     per_iter = 4 * p0.d * p0.n + 8 * p0.m
     peak, peak_kind = measured_peaks()
     roof = None
@@ -798,7 +880,8 @@ def run_ccs(args):
     launches_k, ms_k = ktimes.get(main, (0, 0.0))
     if launches_k:
         avg_s = ms_k / launches_k / 1000.0
-        bytes_per_launch = per_iter * (statistics.mean(iters) if main == "persistent" else 1)
+        bytes_per_launch = (decode_bytes(p0, statistics.mean(iters)) if main == "persistent"
+                            else per_iter)
         achieved = bytes_per_launch / avg_s / 1e9
         roof = {"bound": "hbm", "kernel": main, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
@@ -834,6 +917,10 @@ def run_ccs(args):
     if args.undersampling > 0:
         sweep = undersampling_sweep(ccs, dev, args.undersampling, measured_peaks()[0],
                                     seed=1000 * rank + 20151508)
+    table3 = None
+    if args.table3 > 0:
+        table3 = table3_rows(ccs, dev, args.table3, measured_peaks()[0],
+                             seed=1000 * rank + 3003)
 
     if rank == 0:
         cb = None
@@ -844,10 +931,10 @@ def run_ccs(args):
                 "ms_per_step": 1000.0 * total_s / decodes, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": vs_baseline(args.workload, p0, value),
                 "dtype": "f64", "data": "synthetic",
-                "config": dict(workload_config(args.workload, p0), engine=args.engine,
-                               schedule=args.schedule,
-                               l2="flushed between steps (512 MB write)",
+                "config": dict(workload_config(args.workload, p0),
                                parallelism=f"replicas{world}"),
+                "launch": {"engine": args.engine, "schedule": args.schedule},
+                "decodes_per_step": 1,
                 "e2e": {"value": e2e_value, "unit": "decodes/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches,
@@ -861,6 +948,7 @@ def run_ccs(args):
                 "batched": batched,
                 "serving": serving,
                 "undersampling": sweep,
+                "table3": table3,
                 "alpha_sweep": alphas,
                 "phase_transition": phases,
                 "wall_s_timed_region": wall}
@@ -875,7 +963,7 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ccs", choices=["ccs", "reference"])
-    ap.add_argument("--workload", default="at-scale",
+    ap.add_argument("--workload", default="extreme",
                     choices=["at-scale", "small", "extreme", "table3"])
     ap.add_argument("--engine", type=int, default=0)
     ap.add_argument("--schedule", type=int, default=0,
@@ -894,6 +982,8 @@ def main():
                     help="reduced phase-transition sweep (0: skip)")
     ap.add_argument("--undersampling", type=int, default=3,
                     help="timed decodes per point of the n/m ~ 10^3 sweep (0: skip)")
+    ap.add_argument("--table3", type=int, default=30,
+                    help="problems per size of the Table 3 rows, n = 2^22, 2^24, 2^26 (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

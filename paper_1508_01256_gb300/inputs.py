@@ -90,7 +90,9 @@ def values(k: int, seed: int, model: str = "gauss-grid", band: float = 0.0) -> n
 
 @dataclasses.dataclass
 class Problem:
-    """One synthetic instance: sizes, expander seed and the dense signal x."""
+    """One synthetic instance: sizes, expander seed and the signal x, kept as
+    its support ``idx`` (ascending) and values ``val``; ``x`` is the dense
+    vector, built on first use."""
     n: int
     m: int
     d: int
@@ -98,21 +100,39 @@ class Problem:
     seed: int
     model: str
     a_seed: int
-    x: np.ndarray  # float64[n]
+    idx: np.ndarray  # int64[k]
+    val: np.ndarray  # float64[k]
+    _x: np.ndarray | None = dataclasses.field(default=None, repr=False, compare=False)
+
+    @property
+    def x(self) -> np.ndarray:
+        """Dense float64[n] signal."""
+        if self._x is None:
+            x = np.zeros(self.n, dtype=np.float64)
+            x[self.idx] = self.val
+            self._x = x
+        return self._x
 
     @property
     def support(self) -> np.ndarray:
-        return np.nonzero(self.x)[0]
+        return self.idx
+
+    def x_device(self, device="cuda"):
+        """The dense signal as a device tensor, scattered on the device from
+        the support and values (no dense host copy)."""
+        import torch
+        x = torch.zeros(self.n, dtype=torch.float64, device=device)
+        x[torch.from_numpy(self.idx).to(device)] = torch.from_numpy(self.val).to(device)
+        return x
 
 
 def make_problem(n: int, m: int, d: int, k: int, seed: int,
                  model: str = "gauss-grid", band: float = 0.0) -> Problem:
     if not (1 <= d <= m) or n < 1:
         raise ValueError(f"bad sizes n={n} m={m} d={d}")
-    x = np.zeros(n, dtype=np.float64)
     s = support(n, k, seed)
-    x[s] = values(k, seed, model, band)
-    return Problem(n, m, d, k, seed, model, expander_seed(seed), x)
+    v = values(k, seed, model, band)
+    return Problem(n, m, d, k, seed, model, expander_seed(seed), s, v)
 
 
 # ---------------------------------------------------------------------------
