@@ -63,12 +63,15 @@ def workload_config(name: str, p) -> dict:
                   "flushed between steps (512 MB write)"}
 
 
-def decode_bytes(p, iterations: int) -> int:
-    """Algorithmic bytes of one decode: per iteration 4dn (every column's d
-    row indices) + 8m (one read of r by the score) + 16m (y and r by the
-    residual); once, 8n (writing x_hat) and 16 k (the updates of the k
-    support columns, a lower bound of the accepted pairs)."""
-    return iterations * (4 * p.d * p.n + 24 * p.m) + 8 * p.n + 16 * p.k
+def decode_bytes(p, iterations, row_driven=0, row_entries=0) -> float:
+    """Algorithmic bytes of one decode.  A column-stream iteration moves 4dn
+    (every column's d row indices) + 8m (one read of r by the score) + 16m
+    (y and r by the residual); a row-driven iteration moves 4 bytes per CSR
+    entry of the nonzero rows (row_entries over all of them) + 24m.  Once:
+    8n (writing x_hat) and 16k (the updates of the k support columns, a
+    lower bound of the accepted pairs)."""
+    return ((iterations - row_driven) * (4 * p.d * p.n + 24 * p.m) + row_driven * 24 * p.m +
+            4 * row_entries + 8 * p.n + 16 * p.k)
 
 
 def vs_baseline(name: str, p, value: float):
@@ -320,11 +323,12 @@ def undersampling_sweep(ccs, dev, reps: int, peak: float, seed: int):
         ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
         last = res[-1]
         it = last.iterations
-        alg = decode_bytes(p, it)
+        alg = decode_bytes(p, it, last.row_driven, last.row_entries)
         gbs = alg / (ms * 1e-3) / 1e9
         x_out = ccs.unscale(sc, x_hat) if scaled else x_hat
         entry = {"n": p.n, "m": p.m, "d": p.d, "k": p.k, "rho": rho, "values": model,
                  "ms_per_decode": ms, "decodes_per_s": 1000.0 / ms, "iterations": it,
+                 "row_driven_iterations": last.row_driven, "row_entries": last.row_entries,
                  "status": names.get(last.status, last.status),
                  "exact_recovery": bool(last.status == ccs.CONVERGED and
                                         torch.equal(x_out, x_dev)),
@@ -378,7 +382,8 @@ def table3_rows(ccs, dev, problems: int, peak: float, seed: int):
                 conv += 1
                 ms = e0.elapsed_time(e1)
                 ms_ok.append(ms)
-                alg.append(decode_bytes(p, res.iterations) / (ms * 1e-3) / 1e9)
+                alg.append(decode_bytes(p, res.iterations, res.row_driven, res.row_entries) /
+                           (ms * 1e-3) / 1e9)
                 exact += bool(torch.equal(x_hat, xd))
             del csc, ptr, cols, y, xd
         del x_hat, r, ws
@@ -572,140 +577,135 @@ def batched_vs_plain(ccs, dev, count: int, seed: int, reps: int = 3):
                         "autotuned (1: 1024 threads, 2: 512, 3: 768 a CTA)"}
 
 
-def latency_summary(ccs, infos) -> dict:
-    """p50 / p99 / max latency (ms) of served requests, overall and over the
-    converged ones (requests that do not converge run to max_iter = 100
-    iterations and set the tail)."""
-    lat = sorted(1000.0 * (i.done_s - i.submit_s) for i in infos)
-    conv = sorted(1000.0 * (i.done_s - i.submit_s) for i in infos
-                  if i.result.status == ccs.CONVERGED)
-
-    def pct(v, f):
-        return v[min(len(v) - 1, int(f * len(v)))] if v else None
-    return {"p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "max_ms": lat[-1],
-            "converged_requests": len(conv), "p50_ms_converged": pct(conv, 0.5),
-            "p99_ms_converged": pct(conv, 0.99)}
-
-
 SERVE_LOADS = (0.5, 0.6, 0.7, 0.8, 0.9, 1.0)
 
 
-def serving_run(ccs, dev, count: int, seed: int, load: float = 0.7,
-                pool_bytes: int = 8 << 30, max_batch: int = 512, iters_per_round: int = 2,
-                sweep_requests: int = 0):
-    """Serving workload: `count` distinct requests, n log-uniform 2^12..2^22,
-    delta, rho as in the batched workload, d in {7, 9}.  First all of them at
-    once (the server's peak decodes/s), then Poisson arrivals at `load` x that
-    rate; latency = result ready - submission, from the library's clock.
-    With sweep_requests > 0, an open-loop load sweep follows: at each load in
-    SERVE_LOADS, sweep_requests Poisson arrivals cycle through the distinct
-    problems (request q decodes problem q mod count into its own output slot
-    of a ring), each on a fresh server."""
+def serving_run(ccs, dev, count: int, seed: int, pool_bytes: int = 16 << 30,
+                max_batch: int = 512, iters_per_round: int = 2, oracle_checks: int = 6):
+    """Serving workload (config 5) with seeded requests: `count` distinct
+    requests, n log-uniform 2^12..2^22, delta and rho as in the batched
+    workload, d in {7, 9}.  Each request hands the server its expander seed
+    and host y; the server draws A into its pool at admission, decodes, and
+    copies x_hat back to a host buffer, so the pool (`pool_bytes`) bounds
+    every byte a request holds on the device.  First a closed-loop burst of
+    a sixth of the requests gives the peak decodes/s; then the rest arrive
+    as open-loop Poisson streams at each load in SERVE_LOADS x that peak,
+    an equal share per load, each on a fresh server.  Latency = host buffer
+    filled - submission, from the library's clock.  Every result is checked
+    for exact recovery against x; a sample is decoded alone on the GPU and
+    the smallest ones by the oracle, bit for bit."""
     import random
 
     import numpy as np
     import torch
 
     from paper_1508_01256_gb300 import inputs
+    t_setup = time.perf_counter()
     shapes = inputs.batch_shapes(count, seed=seed, log2n_hi=22.0, ds=(7, 9))
-    reqs, probs = [], []
+    probs, reqs = [], []
     for q, (n, m, d, k) in enumerate(shapes):
         p = inputs.make_problem(n, m, d, k, seed * 7919 + q)
         csc, ptr, cols = ccs.make_expander(p.n, p.m, p.d, p.a_seed, device=dev)
-        y = ccs.measure(ptr, cols, torch.from_numpy(p.x).to(dev), p.m, p.d)
-        reqs.append((csc, ptr, cols, y, torch.empty(p.n, dtype=torch.float64, device=dev),
-                     torch.empty(p.m, dtype=torch.float64, device=dev)))
+        y = ccs.measure(ptr, cols, p.x_device(dev), p.m, p.d).cpu().numpy()
         probs.append(p)
-    torch.cuda.synchronize()
-    with ccs.Server(pool_bytes, max_batch=max_batch, iters_per_round=iters_per_round) as srv:
-        infos = ccs.serve_poisson(srv, reqs, [0.0] * count)
-        closed = count / (max(i.done_s for i in infos) - min(i.submit_s for i in infos))
-        rate = load * closed
-        rng = np.random.default_rng(seed)
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
-        infos = ccs.serve_poisson(srv, reqs, arrivals)
-        st = srv.stats()
-    lat_ms = sorted(1000.0 * (i.done_s - i.submit_s) for i in infos)
-    span = max(i.done_s for i in infos) - min(i.submit_s for i in infos)
-    # each served result equals the request decoded alone (a sample)
-    same = True
-    for q in random.Random(seed).sample(range(count), min(12, count)):
-        csc, ptr, cols, y, x_hat, r = reqs[q]
-        alone = ccs.decode_parallel_l0(csc, ptr, cols, y, history=False)
-        res = infos[q].result
-        same &= (res.status, res.iterations, res.r0_final) == \
-            (alone.status, alone.iterations, alone.r0_final)
-        same &= bool(torch.equal(x_hat, alone.x_hat)) and bool(torch.equal(r, alone.r))
-    exact = sum(int(i.result.status == ccs.CONVERGED and
-                    bool((reqs[q][4].cpu().numpy() == probs[q].x).all()))
-                for q, i in enumerate(infos))
-    # requests that do not converge run to max_iter (100 iterations): they set
-    # the tail of the latency distribution, so the converged ones are also
-    # reported on their own
-    lat_conv = sorted(1000.0 * (i.done_s - i.submit_s) for i in infos
-                      if i.result.status == ccs.CONVERGED)
-    sweep = load_sweep(ccs, dev, reqs, [i.result for i in infos], closed, sweep_requests,
-                       seed, pool_bytes, max_batch, iters_per_round) if sweep_requests > 0 else None
-    return {"requests": count, "offered_rate_per_s": rate, "load": load,
-            "peak_decodes_per_s": closed, "decodes_per_s": count / span,
-            "p50_ms": lat_ms[len(lat_ms) // 2], "p99_ms": lat_ms[min(len(lat_ms) - 1,
-                                                                  int(0.99 * len(lat_ms)))],
-            "max_ms": lat_ms[-1],
-            "converged_requests": len(lat_conv),
-            "p50_ms_converged": lat_conv[len(lat_conv) // 2] if lat_conv else None,
-            "p99_ms_converged": lat_conv[min(len(lat_conv) - 1, int(0.99 * len(lat_conv)))]
-            if lat_conv else None,
-            "rounds": st["rounds"], "peak_inflight": st["peak_inflight"],
-            "peak_state_bytes": st["peak_bytes"], "pool_bytes": pool_bytes,
-            "iters_per_round": iters_per_round, "same_results_sample": same,
-            "exact_recovery": exact,
-            "workload": "n log-uniform 2^12..2^22, m/n in {0.01,0.05,0.1,0.3}, "
-                        "k/m in {0.05,0.1,0.2}, d in {7,9}, Poisson arrivals",
-            "load_sweep": sweep}
-
-
-def load_sweep(ccs, dev, reqs, base, peak: float, count: int, seed: int, pool_bytes: int,
-               max_batch: int, iters_per_round: int) -> dict:
-    """Open-loop Poisson load sweep over SERVE_LOADS x `peak` (the closed-loop
-    decodes/s of the same request mix).  Request q decodes distinct problem
-    q mod D into output slot q mod R (R a multiple of D, so a slot always
-    holds the same problem's shape); a slot is reused only after its earlier
-    request was collected.  Every served result (status, iterations, final
-    ||r||_0) is checked against the same problem's result in the distinct
-    run."""
-    import numpy as np
-    import torch
-
-    D = len(reqs)
-    R = D * max(1, min(8, -(-count // D)))
-    outs = [(torch.empty_like(reqs[s % D][4]), torch.empty_like(reqs[s % D][5]))
-            for s in range(R)]
-
-    def request_of(q):
-        csc, ptr, cols, y = reqs[q % D][:4]
-        return (csc, ptr, cols, y) + outs[q % R]
-
-    points = []
-    rng = np.random.default_rng(seed + 1)
-    for load in SERVE_LOADS:
-        rate = load * peak
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
-        with ccs.Server(pool_bytes, max_batch=max_batch, iters_per_round=iters_per_round) as srv:
-            infos, waited = ccs.serve_stream(srv, request_of, count, arrivals, R)
-            st = srv.stats()
-        span = max(i.done_s for i in infos) - min(i.submit_s for i in infos)
-        same = all((i.result.status, i.result.iterations, i.result.r0_final) ==
-                   (base[q % D].status, base[q % D].iterations, base[q % D].r0_final)
-                   for q, i in enumerate(infos))
-        points.append(dict({"load": load, "offered_rate_per_s": rate,
-                            "decodes_per_s": count / span}, **latency_summary(ccs, infos),
-                           peak_inflight=st["peak_inflight"], rounds=st["rounds"],
-                           peak_state_bytes=st["peak_bytes"], slot_waits=waited,
-                           same_results=same))
-    del outs
+        reqs.append((p.n, p.m, p.d, p.a_seed, y))
+        del csc, ptr, cols
     torch.cuda.empty_cache()
-    return {"requests_per_load": count, "distinct_problems": D, "output_slots": R,
-            "peak_decodes_per_s": peak, "points": points}
+    setup_s = time.perf_counter() - t_setup
+    rng = random.Random(seed)
+    keep = set(rng.sample(range(count), min(12, count)))
+    small = [q for q in range(count) if probs[q].n <= 2 ** 15]
+    oracle_q = set(rng.sample(small, min(oracle_checks, len(small))))
+    kept = {}
+    tally = {"converged": 0, "exact": 0}
+
+    def on_done(q, info, x_hat):
+        p = probs[q]
+        ok = info.result.status == ccs.CONVERGED and info.result.error == 0
+        tally["converged"] += ok
+        tally["exact"] += bool(ok and np.count_nonzero(x_hat) == p.k and
+                               np.array_equal(x_hat[p.idx], p.val))
+        if q in keep or q in oracle_q:
+            kept[q] = (info.result, x_hat)
+
+    def run(qs, arrivals):
+        timeline = []
+        with ccs.Server(pool_bytes, max_batch=max_batch, iters_per_round=iters_per_round) as srv:
+            infos = ccs.serve_seeded(srv, [reqs[q] for q in qs], arrivals,
+                                     lambda i, info, x: on_done(qs[i], info, x),
+                                     sampler=timeline)
+            st = srv.stats()
+        lat = sorted(1000.0 * (i.done_s - i.submit_s) for i in infos)
+        conv = sorted(1000.0 * (i.done_s - i.submit_s) for i in infos
+                      if i.result.status == ccs.CONVERGED)
+
+        def pct(v, f):
+            return v[min(len(v) - 1, int(f * len(v)))] if v else None
+        span = max(i.done_s for i in infos) - min(i.submit_s for i in infos)
+        infl = [t[1] for t in timeline]
+        step = max(1, len(timeline) // 16)
+        return {"requests": len(qs), "decodes_per_s": len(qs) / span,
+                "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "max_ms": lat[-1],
+                "converged_requests": len(conv), "p50_ms_converged": pct(conv, 0.5),
+                "p99_ms_converged": pct(conv, 0.99), "rounds": st["rounds"],
+                "peak_inflight": st["peak_inflight"], "peak_pool_bytes": st["peak_bytes"],
+                "mean_inflight": statistics.mean(infl) if infl else None,
+                "inflight_over_time": [(round(t[0], 4), t[1], t[2]) for t in timeline[::step]],
+                "errors": sum(i.result.error != 0 for i in infos)}
+
+    n_closed = max(1, count // 6)
+    closed_q = list(range(n_closed))
+    closed = run(closed_q, [0.0] * n_closed)
+    peak = closed["decodes_per_s"]
+    rest = list(range(n_closed, count))
+    per = max(1, len(rest) // len(SERVE_LOADS))
+    points = []
+    arr_rng = np.random.default_rng(seed + 1)
+    for li, load in enumerate(SERVE_LOADS):
+        qs = rest[li * per:(li + 1) * per] if li < len(SERVE_LOADS) - 1 else rest[li * per:]
+        if not qs:
+            break
+        arrivals = np.cumsum(arr_rng.exponential(1.0 / (load * peak), size=len(qs)))
+        pt = run(qs, arrivals)
+        pt.update(load=load, offered_rate_per_s=load * peak)
+        points.append(pt)
+    # each sampled result equals the same decode alone on the GPU, and the
+    # smallest ones the oracle's decode, bit for bit
+    same_alone = True
+    for q in sorted(keep):
+        p = probs[q]
+        res, x_hat = kept[q]
+        csc, ptr, cols = ccs.make_expander(p.n, p.m, p.d, p.a_seed, device=dev)
+        alone = ccs.decode_parallel_l0(csc, ptr, cols, torch.from_numpy(reqs[q][4]).to(dev),
+                                       history=False)
+        same_alone &= (res.status, res.iterations, res.r0_final) == \
+            (alone.status, alone.iterations, alone.r0_final)
+        same_alone &= bool(np.array_equal(x_hat, alone.x_hat.cpu().numpy()))
+        del csc, ptr, cols, alone
+    same_oracle = None
+    if oracle_q:
+        import oracle
+        same_oracle = True
+        for q in sorted(oracle_q):
+            p = probs[q]
+            res, x_hat = kept[q]
+            A = oracle.make_expander(p.n, p.m, p.d, p.a_seed)
+            ref = oracle.parallel_l0(A, p.m, reqs[q][4])
+            same_oracle &= (res.status, res.iterations, res.r0_final) == \
+                (ref["status"], ref["iterations"], ref["r0_final"])
+            same_oracle &= bool(np.array_equal(x_hat.view(np.int64), ref["x_hat"].view(np.int64)))
+    torch.cuda.empty_cache()
+    return {"requests": count, "distinct": True, "pool_bytes": pool_bytes,
+            "max_batch": max_batch, "iters_per_round": iters_per_round,
+            "closed_loop": closed, "peak_decodes_per_s": peak, "load_sweep": points,
+            "converged": tally["converged"], "exact_recovery": tally["exact"],
+            "same_as_alone_sample": same_alone, "sample_size": len(keep),
+            "same_as_oracle_sample": same_oracle, "oracle_sample_size": len(oracle_q),
+            "setup_s": setup_s,
+            "workload": "seeded requests (the server draws A from the seed into its pool): "
+                        "n log-uniform 2^12..2^22, m/n in {0.01,0.05,0.1,0.3}, k/m in "
+                        "{0.05,0.1,0.2}, d in {7,9}, gauss-grid; closed-loop burst of "
+                        "count/6, then Poisson arrivals at 0.5-1.0x its rate"}
 
 
 def run_reference(args):
@@ -880,8 +880,9 @@ def run_ccs(args):
     launches_k, ms_k = ktimes.get(main, (0, 0.0))
     if launches_k:
         avg_s = ms_k / launches_k / 1000.0
-        bytes_per_launch = (decode_bytes(p0, statistics.mean(iters)) if main == "persistent"
-                            else per_iter)
+        bytes_per_launch = (statistics.mean(decode_bytes(p0, rr.iterations, rr.row_driven,
+                                                         rr.row_entries) for rr in results)
+                            if main == "persistent" else per_iter)
         achieved = bytes_per_launch / avg_s / 1e9
         roof = {"bound": "hbm", "kernel": main, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
@@ -905,8 +906,7 @@ def run_ccs(args):
         batched = batched_vs_plain(ccs, dev, args.batch, seed=1000 * rank + 4242)
     serving = None
     if args.serve > 0:
-        serving = serving_run(ccs, dev, args.serve, seed=1000 * rank + 777,
-                              sweep_requests=args.serve_sweep)
+        serving = serving_run(ccs, dev, args.serve, seed=1000 * rank + 777)
     alphas = None
     if args.alpha_sweep > 0:
         alphas = alpha_sweep(ccs, dev, seed=1000 * rank + 31)
@@ -943,6 +943,8 @@ def run_ccs(args):
                 "clocks": clk.summary(),
                 "column_updates_per_s": value * p0.n * statistics.mean(iters),
                 "iterations_mean": statistics.mean(iters),
+                "row_driven_iterations_mean": statistics.mean(rr.row_driven for rr in results),
+                "row_entries_mean": statistics.mean(rr.row_entries for rr in results),
                 "exact_recovery": exact,
                 "kernel_times": kernel_share,
                 "batched": batched,
@@ -972,10 +974,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=512,
                     help="problems in the batched-vs-plain comparison (0: skip)")
-    ap.add_argument("--serve", type=int, default=256,
-                    help="requests in the serving run (0: skip)")
-    ap.add_argument("--serve-sweep", type=int, default=10000,
-                    help="requests per load point of the serving load sweep (0: skip)")
+    ap.add_argument("--serve", type=int, default=10000,
+                    help="distinct seeded requests in the serving run: a closed-loop sixth, "
+                         "the rest over the Poisson load sweep (0: skip)")
     ap.add_argument("--alpha-sweep", type=int, default=1,
                     help="alpha in [2, d] under both scores at n = 2^20 (0: skip)")
     ap.add_argument("--phase", type=int, default=1,

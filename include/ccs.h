@@ -109,8 +109,15 @@ typedef struct {
                              instead of by exact atomic updates.  Bit 2: the
                              test that certifies those updates exact is
                              treated as failing from iteration 2, so the
-                             decode switches residual mode mid-way.  Results
-                             are the same for every setting of bits 1, 2.    */
+                             decode switches residual mode mid-way.  Bits
+                             3-5 (persistent engine, one problem per
+                             launch) steer the row-driven score phase: bit 3
+                             scores its candidates one by one instead of
+                             queueing them, bit 4 takes it whenever its row
+                             list fits instead of only once ||r||_0 <= m/32
+                             on a CSC of at least 2^26 entries, bit 5 never
+                             takes it.  Results are the same
+                             for every setting of bits 1-5.                  */
     int32_t schedule;     /* persistent-engine launch shape: 0 = library's
                              choice (1 when d <= 8, else 2); 1 = 1024
                              threads a CTA, one 32-column tile per warp and
@@ -133,7 +140,14 @@ typedef struct {
     int64_t r0_final;     /* ||r||_0 at exit                                   */
     int32_t error;        /* CCS_OK, or the CCS_E* code that ended this
                              problem early (e.g. CCS_ETIMEOUT)               */
-    int32_t reserved;
+    int32_t row_driven;   /* iterations whose score phase was row-driven:
+                             once ||r||_0 <= m/32 on a CSC too large for L2
+                             (n d >= 2^26), the persistent engine (one
+                             problem per launch) finds the columns that can
+                             still be accepted from the CSR rows of the
+                             nonzero r_i instead of streaming every column
+                             (same results)                                  */
+    int64_t row_entries;  /* CSR entries those score phases read            */
 } ccs_result;
 
 /* One problem of a batch: sizes and caller-owned device arrays. */
@@ -374,6 +388,29 @@ typedef struct {
     int32_t reserved;
 } ccs_server_stats;
 
+/* A request whose device memory the server owns (not in the paper).  The
+ * caller gives the expander's seed and HOST buffers; at admission the server
+ * draws A into the pool from (n, m, d, a_seed) exactly as ccs_make_expander
+ * does and copies y from the host, so everything the request keeps on the
+ * device -- A as CSC and CSR, y, x_hat, r, the ||r||_0 history and the
+ * decode state, ccs_seeded_request_bytes() in all -- comes out of the pool,
+ * and the pool bounds the server's HBM.  When the decode ends, x_hat (and
+ * r, r0_hist when non-null) are copied to the host buffers before the
+ * result is published and the memory returns to the pool.  The host
+ * buffers must stay valid, and y unchanged, until the result is collected.
+ * Results are bit-identical to ccs_decode_parallel_l0 on the same A and y. */
+typedef struct {
+    int32_t n, m, d, reserved;
+    uint64_t a_seed;          /* seed of A, as for ccs_make_expander         */
+    const double *y;          /* HOST, m measurements                        */
+    double *x_hat;            /* HOST out, n                                 */
+    double *r;                /* HOST out, m: y - A x_hat at exit; optional  */
+    int64_t *r0_hist;         /* HOST out, max_iter+1 entries; optional      */
+} ccs_seeded_request;
+
+/* Pool bytes one seeded request holds while admitted (0: invalid sizes). */
+CCS_API size_t ccs_seeded_request_bytes(int32_t n, int32_t m, int32_t d, int32_t max_iter);
+
 /* Starts the worker on the current device; work goes to `stream`.
  * CCS_EINVAL for a bad configuration, CCS_EBUDGET if the pool cannot even
  * hold the launch header. */
@@ -382,6 +419,12 @@ CCS_API int ccs_server_create(const ccs_server_config *cfg, ccs_stream_t stream,
 /* Queues a request; *ticket identifies it.  CCS_EBUDGET if its state can
  * never fit the pool, CCS_EINVAL for bad sizes or arrays. */
 CCS_API int ccs_server_submit(ccs_server *s, const ccs_problem *req, int64_t *ticket);
+/* Queues a seeded request (see ccs_seeded_request).  CCS_EBUDGET if
+ * ccs_seeded_request_bytes() can never fit the pool, CCS_EINVAL for bad
+ * sizes or null y / x_hat.  A failure while drawing A or copying data ends
+ * the request with that code in its result's error field. */
+CCS_API int ccs_server_submit_seeded(ccs_server *s, const ccs_seeded_request *req,
+                                     int64_t *ticket);
 /* CCS_OK and *info once the request has finished (the ticket is then
  * released); CCS_EBUSY while it is pending or running. */
 CCS_API int ccs_server_poll(ccs_server *s, int64_t ticket, ccs_ticket_info *info);

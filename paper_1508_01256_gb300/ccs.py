@@ -47,7 +47,7 @@ class Params(ctypes.Structure):
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
                 ("r0_final", ctypes.c_int64), ("error", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("row_driven", ctypes.c_int32), ("row_entries", ctypes.c_int64)]
 
 
 class Problem(ctypes.Structure):
@@ -56,6 +56,13 @@ class Problem(ctypes.Structure):
                 ("csc_rows", ctypes.c_void_p), ("csr_ptr", ctypes.c_void_p),
                 ("csr_cols", ctypes.c_void_p), ("y", ctypes.c_void_p),
                 ("x_hat", ctypes.c_void_p), ("r", ctypes.c_void_p),
+                ("r0_hist", ctypes.c_void_p)]
+
+
+class SeededRequest(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32), ("d", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("a_seed", ctypes.c_uint64),
+                ("y", ctypes.c_void_p), ("x_hat", ctypes.c_void_p), ("r", ctypes.c_void_p),
                 ("r0_hist", ctypes.c_void_p)]
 
 
@@ -141,11 +148,16 @@ def lib() -> ctypes.CDLL:
         l.ccs_noalloc_scratch_bytes.restype = sz
         l.ccs_server_create.argtypes = [ctypes.POINTER(ServerConfig), P, ctypes.POINTER(P)]
         l.ccs_server_submit.argtypes = [P, ctypes.POINTER(Problem), ctypes.POINTER(i64)]
+        l.ccs_server_submit_seeded.argtypes = [P, ctypes.POINTER(SeededRequest),
+                                               ctypes.POINTER(i64)]
+        l.ccs_seeded_request_bytes.argtypes = [i32, i32, i32, i32]
+        l.ccs_seeded_request_bytes.restype = sz
         l.ccs_server_poll.argtypes = [P, i64, ctypes.POINTER(TicketInfo)]
         l.ccs_server_wait.argtypes = [P, i64, ctypes.POINTER(TicketInfo), i32]
         l.ccs_server_stats_get.argtypes = [P, ctypes.POINTER(ServerStats)]
         l.ccs_server_destroy.argtypes = [P]
-        for name in ("ccs_server_create", "ccs_server_submit", "ccs_server_poll",
+        for name in ("ccs_server_create", "ccs_server_submit", "ccs_server_submit_seeded",
+                     "ccs_server_poll",
                      "ccs_server_wait", "ccs_server_stats_get", "ccs_server_destroy"):
             getattr(l, name).restype = ctypes.c_int
         l.ccs_batch_graph_create.argtypes = [ctypes.POINTER(Problem), i32, ctypes.POINTER(Params),
@@ -367,6 +379,10 @@ def ccs_decode_parallel_l0_noalloc(n, m, d, csc_rows, csr_ptr, csr_cols, y, x_ha
     return out
 
 
+def ccs_seeded_request_bytes(n: int, m: int, d: int, max_iter: int = 100) -> int:
+    return int(lib().ccs_seeded_request_bytes(n, m, d, max_iter))
+
+
 def ccs_noalloc_scratch_bytes() -> int:
     return int(lib().ccs_noalloc_scratch_bytes())
 
@@ -499,7 +515,8 @@ def decode_parallel_l0(csc_rows, csr_ptr, csr_cols, y, alpha=2, max_iter=100,
                                  ws, stream)
     h = hist[:res.iterations + 1].cpu().tolist() if hist is not None else None
     return DecodeOutput(x_hat=x_hat, r=r, r0_hist=h, status=res.status,
-                        iterations=res.iterations, r0_final=res.r0_final, error=res.error)
+                        iterations=res.iterations, r0_final=res.r0_final, error=res.error,
+                        row_driven=res.row_driven, row_entries=res.row_entries)
 
 
 def problem(csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist=None,
@@ -606,6 +623,34 @@ class Server:
         _check(lib().ccs_server_submit(self._h, ctypes.byref(pb), ctypes.byref(t)),
                "ccs_server_submit")
         self._keep[t.value] = (csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist)
+        return t.value
+
+    def submit_seeded(self, n: int, m: int, d: int, a_seed: int, y, x_hat, r=None,
+                      r0_hist=None) -> int:
+        """A request whose A the server draws from `a_seed` into its pool
+        (ccs_server_submit_seeded).  y, x_hat, r, r0_hist are HOST numpy
+        arrays (float64 m, float64 n, float64 m, int64 >= max_iter + 1),
+        kept alive here until the result is collected."""
+        import numpy as np
+
+        def need(a, dtype, size, name, at_least=False):
+            if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous \
+                    or (a.size < size if at_least else a.size != size):
+                raise ValueError(f"{name}: need a contiguous {np.dtype(dtype)} numpy array "
+                                 f"of {'at least ' if at_least else ''}{size} elements")
+        need(y, np.float64, m, "y")
+        need(x_hat, np.float64, n, "x_hat")
+        if r is not None:
+            need(r, np.float64, m, "r")
+        if r0_hist is not None:
+            need(r0_hist, np.int64, self.max_iter + 1, "r0_hist", at_least=True)
+        req = SeededRequest(n, m, d, 0, a_seed & (2 ** 64 - 1), y.ctypes.data, x_hat.ctypes.data,
+                            r.ctypes.data if r is not None else None,
+                            r0_hist.ctypes.data if r0_hist is not None else None)
+        t = ctypes.c_int64()
+        _check(lib().ccs_server_submit_seeded(self._h, ctypes.byref(req), ctypes.byref(t)),
+               "ccs_server_submit_seeded")
+        self._keep[t.value] = (y, x_hat, r, r0_hist)
         return t.value
 
     def poll(self, ticket: int):
@@ -726,3 +771,67 @@ def serve_stream(server: Server, request_of, count: int, arrivals_s, ring: int,
     if state["error"] is not None:
         raise state["error"]
     return infos, waited
+
+
+def serve_seeded(server: Server, requests, arrivals_s, on_done, timeout_ms: int = 120000,
+                 sampler=None, sample_every_s: float = 0.002):
+    """Open-loop serving of seeded requests: requests[q] = (n, m, d, a_seed,
+    y host array) is submitted at arrivals_s[q] (seconds from now) with a
+    fresh host x_hat buffer; when its result arrives (collected in
+    submission order) on_done(q, info, x_hat) is called and the buffer is
+    released.  With `sampler` (a list), (t, inflight, pending, bytes_in_use)
+    from ccs_server_stats is appended every `sample_every_s` while requests
+    are outstanding.  Returns the TicketInfo list in submission order."""
+    import time
+
+    import numpy as np
+    count = len(requests)
+    tickets, bufs, infos = [], {}, [None] * count
+    state = {"error": None, "done": False}
+
+    def collect():
+        try:
+            for i in range(count):
+                while i >= len(tickets):
+                    if state["error"] is not None:
+                        return
+                    time.sleep(0.0001)
+                info = server.wait(tickets[i], timeout_ms)
+                if info is None:
+                    raise RuntimeError(f"request {i} not finished within {timeout_ms} ms")
+                infos[i] = info
+                on_done(i, info, bufs.pop(i))
+        except BaseException as e:  # re-raised on the submitting thread
+            state["error"] = e
+        finally:
+            state["done"] = True
+
+    def sample(t0):
+        while not state["done"]:
+            st = server.stats()
+            sampler.append((time.perf_counter() - t0, st["inflight"], st["pending"],
+                            st["bytes_in_use"]))
+            time.sleep(sample_every_s)
+
+    th = threading.Thread(target=collect, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    ts = None
+    if sampler is not None:
+        ts = threading.Thread(target=sample, args=(t0,), daemon=True)
+        ts.start()
+    for q, (n, m, d, a_seed, y) in enumerate(requests):
+        delay = t0 + arrivals_s[q] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        if state["error"] is not None:
+            break
+        x = np.empty(n, dtype=np.float64)
+        bufs[q] = x
+        tickets.append(server.submit_seeded(n, m, d, a_seed, y, x))
+    th.join()
+    if ts is not None:
+        ts.join()
+    if state["error"] is not None:
+        raise state["error"]
+    return infos

@@ -229,7 +229,8 @@ int decode_host_loop(const ProblemDev &P, const ccs_params &p, ccs_result *out,
     out->iterations = h.iteration;
     out->r0_final = h.r0;
     out->error = (h.error & kErrWatchdog) ? CCS_ETIMEOUT : CCS_OK;
-    out->reserved = 0;
+    out->row_driven = 0;
+    out->row_entries = 0;
     return out->error;
 }
 

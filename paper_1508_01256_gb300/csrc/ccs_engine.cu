@@ -369,7 +369,8 @@ int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, c
         out[p].iterations = hc.iteration;
         out[p].r0_final = hc.r0;
         out[p].error = herr ? CCS_ETIMEOUT : CCS_OK;
-        out[p].reserved = 0;
+        out[p].row_driven = hc.row_driven;
+        out[p].row_entries = hc.row_entries;
         max_it = std::max(max_it, hc.iteration);
     }
     if (a.stamps) prof_keep_stamps(hst.data(), (int)hst.size(), kSubBase);

@@ -53,9 +53,16 @@ constexpr int kMinQueue = 256;      // fewest (more go through the inline exact 
 constexpr int kFlagSkipArrive = 1;  // test hook: CTA 0 never arrives at barrier 1
 constexpr int kFlagOrdered = 2;     // test hook: ordered residual from the start
 constexpr int kFlagSwitch = 4;      // test hook: the certificate fails from iteration 2
+constexpr int kFlagRowInline = 8;   // test hook: row-driven candidates scored inline, no queue
+constexpr int kFlagRowAlways = 16;  // test hook: row-driven whenever the row list fits
+constexpr int kFlagRowNever = 32;   // every score phase streams the CSC
 constexpr int kFpChunk = 32768;     // bytes per fingerprint bulk copy
 constexpr int kWbufPerWarp = 32;    // buffered candidate columns per consumer warp
 constexpr int kSubBase = 3 * kMaxStampIters + 2;  // CTA-0 score sub-phase stamps start here
+constexpr int kRowDrivenDiv = 32;   // row-driven score phase while ||r||_0 <= m / kRowDrivenDiv
+constexpr long long kRowDrivenMinEntries = 64ll << 20;  // ... and the CSC (n d entries) streams
+                                                       // from HBM, not from L2
+constexpr int kRowUnroll = 16;      // CSR entries in flight per thread in that phase
 
 struct Segment {
     int prob, lo, hi, pad;  // tiles [lo, hi) of problem `prob`
@@ -513,6 +520,8 @@ __device__ __forceinline__ bool queue_or_score(const EngineArgs &a, const Proble
     if (q < a.queue_cap) {  // scored after the stream
         int32_t *e = queue + q * (DMAX + 1);
         e[0] = j;
+        // x_hat_j is read when the queue is scored: bring its line into L2 now
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(P.x_hat + j));
 #pragma unroll
         for (int t = 0; t < DMAX; ++t) e[1 + t] = rows[t];
         return false;
@@ -678,6 +687,26 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
 // (contributor records), 2 in the iteration that switches from 0 to 1 (the
 // segment's nonzero columns enter their rows' records first).  it: the
 // problem's own iteration number.
+// Switch of a segment to the ordered residual: its columns that are already
+// nonzero enter their rows' contributor records, and every column's in-slots
+// flag is set from x_hat (r itself is exact and current, so no row is marked
+// touched).
+template <int DMAX>
+__device__ __forceinline__ void enter_segment_slots(const ProblemDev &P, int seg_lo, int seg_hi) {
+    const long long c1 = min((long long)P.n, (long long)seg_hi * kTile);
+    for (long long j = (long long)seg_lo * kTile + threadIdx.x; j < c1; j += blockDim.x) {
+        const bool nz = __ldcg(P.x_hat + j) != 0.0;
+        P.in_slots[j] = nz ? 1 : 0;
+        if (nz) {
+            int32_t rows[DMAX];
+#pragma unroll
+            for (int t = 0; t < DMAX; ++t)
+                rows[t] = (t < P.d) ? __ldg(P.csc_rows + (size_t)j * P.d + t) : 0;
+            enter_slots<DMAX>(P, (int)j, rows, P.d);
+        }
+    }
+}
+
 template <int DMAX, int THREADS>
 __device__ __forceinline__ void score_segment(const EngineArgs &a, const ProblemDev &P,
                                               int seg_lo, int seg_hi, int g, int it, int rmode,
@@ -702,22 +731,7 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
         *S.acc = 0;
         *S.xmax = 0;
     }
-    if (rmode == 2) {
-        // switch to the ordered residual: the segment's columns that are
-        // already nonzero enter their rows' contributor records (r itself is
-        // exact and current, so no row is marked touched)
-        const long long c1 = min((long long)P.n, (long long)seg_hi * kTile);
-        for (long long j = (long long)seg_lo * kTile + threadIdx.x; j < c1; j += blockDim.x) {
-            if (__ldcg(P.x_hat + j) != 0.0) {
-                int32_t rows[DMAX];
-#pragma unroll
-                for (int t = 0; t < DMAX; ++t)
-                    rows[t] = (t < P.d) ? __ldg(P.csc_rows + (size_t)j * P.d + t) : 0;
-                P.in_slots[j] = 1;
-                enter_slots<DMAX>(P, (int)j, rows, P.d);
-            }
-        }
-    }
+    if (rmode == 2) enter_segment_slots<DMAX>(P, seg_lo, seg_hi);
     __syncthreads();
 
     if (warp == 0) {
@@ -780,6 +794,329 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
         if (a.stamps && blockIdx.x == 0 && g < kMaxStampIters)
             a.stamps[kSubBase + 3 * g + 2] = globaltimer();
     }
+}
+
+// ---- row-driven score phase (one problem per launch, small ||r||_0) ---------
+//
+// A column can be accepted only if at least T of its d rows hold a nonzero
+// r_i: its l0 decrease (Eq. 15) is at most (nonzero rows) - (zero rows), so
+// T = ceil((alpha + d) / 2); its match count (Alg. 8) is at most the nonzero
+// rows, so T = alpha.  Once ||r||_0 is small, the columns that reach T are
+// found from the CSR rows of the nonzero r_i -- the CTAs split those rows'
+// entries evenly and count each column's hits in a byte per column -- and
+// only they are scored exactly, as the column stream would score them.
+// Every other column keeps a score below alpha, so the accepted set, and the
+// decode, are the ones of the column stream, bit for bit.  The phase reads
+// the CSR entries of the nonzero rows (||r||_0 * nd/m on average) instead of
+// the whole CSC (4dn bytes).
+
+// Which score phase iteration `it` of a lone problem takes.  Every CTA
+// evaluates it from the same stored ||r||_0, so all agree.  The row list
+// lives in the CSC stage ring (16 bytes a row).  Measured on a GB300, a CSR
+// entry counted by a global atomic costs 35-60 times a column entry of the
+// CSC stream, so the phase pays only while ||r||_0 is a few percent of m,
+// and only when the stream comes from HBM (an L2-resident CSC streams too
+// fast for the phase's fixed cost to pay back).
+__device__ __forceinline__ bool row_driven_iter(const EngineArgs &a, const ProblemDev &P, int it,
+                                                long long r0) {
+    if (a.probs || !(P.flags & kPdUseFp) || it < 1 || r0 <= 0 || (a.debug_flags & kFlagRowNever))
+        return false;
+    const long long cap = ((long long)a.stages * a.stage_bytes - 16) / 16;
+    return r0 <= cap && ((a.debug_flags & kFlagRowAlways) ||
+                         (r0 * kRowDrivenDiv <= (long long)P.m &&
+                          (long long)P.n * P.d >= kRowDrivenMinEntries));
+}
+
+// Row list of a row-driven phase in the stage ring: the nonzero rows in
+// ascending order, the CSR offset of each, and the exclusive prefix of their
+// degrees (pref[R] = E, the entries of all of them).
+struct RowList {
+    long long *ptr0;  // cap
+    int *pref;        // cap + 1
+    int *rows;        // cap
+};
+
+__device__ __forceinline__ RowList row_list(const EngineArgs &a, const ScoreSmem &S) {
+    const int cap = (int)(((long long)a.stages * a.stage_bytes - 16) / 16);
+    RowList L;
+    L.ptr0 = reinterpret_cast<long long *>(S.stage);
+    L.pref = reinterpret_cast<int *>(L.ptr0 + cap);
+    L.rows = L.pref + cap + 1;
+    return L;
+}
+
+// Block-wide exclusive prefix of one int per thread; *total gets the sum.
+template <int THREADS>
+__device__ __noinline__ int block_excl_scan(int v, int *total) {
+    __shared__ int s_w[THREADS / 32];
+    __shared__ int s_tot;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    __syncthreads();  // earlier users of s_w are done
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += s_w[w];
+    if (threadIdx.x == THREADS - 1) s_tot = before + inc;
+    __syncthreads();
+    *total = s_tot;
+    return before + inc - v;
+}
+
+// Nonzero fingerprints in a 32-bit word of the array (2 of 16 bits or 4 of
+// 8 bits); bit t of the mask: entry t of the word.
+template <bool kWide>
+__device__ __forceinline__ unsigned fp_word_mask(unsigned w) {
+    if constexpr (kWide) return ((w & 0xffffu) != 0u) | (((w >> 16) != 0u) << 1);
+    else
+        return ((w & 0xffu) != 0u) | ((((w >> 8) & 0xffu) != 0u) << 1) |
+               ((((w >> 16) & 0xffu) != 0u) << 2) | (((w >> 24) != 0u) << 3);
+}
+
+// Fill the row list from the fingerprints in shared memory (fp_i == 0 iff
+// r_i == 0).  Each warp takes a contiguous run of 32-bit words and its lanes
+// read consecutive words (no bank conflicts); a first pass counts, a block
+// scan places the warps, a second pass writes the rows in ascending order.
+// Returns R (every CTA builds the same list); *E the entries.
+template <int THREADS, bool kWide>
+__device__ __forceinline__ int list_nonzero_rows(const ProblemDev &P, const uint8_t *fp,
+                                                 const RowList &L, int cap, int *E) {
+    constexpr int kW = THREADS / 32, kPer = kWide ? 2 : 4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned *fw = reinterpret_cast<const unsigned *>(fp);
+    const int nw = (P.m + kPer - 1) / kPer;  // words; entries past row m - 1 are masked
+    const unsigned last = (P.m % kPer) ? (1u << (P.m % kPer)) - 1u : (1u << kPer) - 1u;
+    const int w0 = (int)((long long)nw * warp / kW), w1 = (int)((long long)nw * (warp + 1) / kW);
+    auto word_mask = [&](int w) {
+        const unsigned msk = fp_word_mask<kWide>(fw[w]);
+        return w == nw - 1 ? msk & last : msk;
+    };
+    int cnt = 0;
+    for (int w = w0 + lane; w < w1; w += 32) cnt += __popc(word_mask(w));
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    int R;
+    int base = block_excl_scan<THREADS>(lane == 0 ? cnt : 0, &R);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int w0r = w0; w0r < w1; w0r += 32) {
+        const int w = w0r + lane;
+        const unsigned msk = w < w1 ? word_mask(w) : 0u;
+        const int c = __popc(msk);
+        int inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        int k = base + inc - c;
+        for (unsigned b = msk; b; b &= b - 1) {
+            const int i = w * kPer + __ffs(b) - 1;
+            if (k < cap) L.rows[k] = i;
+            ++k;
+        }
+        base += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    R = min(R, cap);  // R == ||r||_0 <= cap by row_driven_iter
+    __syncthreads();
+    const int per2 = (R + THREADS - 1) / THREADS;
+    const int q0 = min(R, (int)threadIdx.x * per2), q1 = min(R, q0 + per2);
+    int sum = 0;
+    for (int q = q0; q < q1; ++q) {
+        const int i = L.rows[q];
+        const long long p0 = __ldg(P.csr_ptr + i), p1 = __ldg(P.csr_ptr + i + 1);
+        L.ptr0[q] = p0;
+        L.pref[q] = (int)(p1 - p0);  // degree for now
+        sum += (int)(p1 - p0);
+    }
+    int off = block_excl_scan<THREADS>(sum, E);
+    for (int q = q0; q < q1; ++q) {
+        const int deg = L.pref[q];
+        L.pref[q] = off;
+        off += deg;
+    }
+    if (threadIdx.x == 0) L.pref[R] = *E;
+    __syncthreads();
+    return R;
+}
+
+// This CTA's share [lo, hi) of the E entries, and the row holding entry f.
+__device__ __forceinline__ void row_share(long long E, long long &lo, long long &hi) {
+    lo = E * blockIdx.x / gridDim.x;
+    hi = E * (blockIdx.x + 1) / gridDim.x;
+}
+
+__device__ __forceinline__ int row_of_entry(const RowList &L, int R, long long f) {
+    int lo = 0, hi = R - 1;  // last q with pref[q] <= f
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (L.pref[mid] <= f) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Visit this CTA's entries: each warp takes a contiguous part of the CTA's
+// share and its lanes read consecutive entries (coalesced), kRowUnroll per
+// lane at a time; fn(cols) gets those column indices (-1 where none),
+// loaded together.  A lane's row cursor moves forward only.
+template <int THREADS, typename F>
+__device__ __forceinline__ void for_my_row_entries(const ProblemDev &P, const RowList &L, int R,
+                                                   long long E, F &&fn) {
+    long long lo, hi;
+    row_share(E, lo, hi);
+    if (hi <= lo || R == 0) return;
+    constexpr int kW = THREADS / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long wlo = lo + (hi - lo) * warp / kW, whi = lo + (hi - lo) * (warp + 1) / kW;
+    if (whi <= wlo) return;
+    long long f0 = wlo + lane;
+    int q = row_of_entry(L, R, f0 < whi ? f0 : wlo);
+    for (; f0 < whi; f0 += 32LL * kRowUnroll) {
+        int cols[kRowUnroll];
+#pragma unroll
+        for (int u = 0; u < kRowUnroll; ++u) {
+            const long long f = f0 + 32LL * u;
+            cols[u] = -1;
+            if (f < whi) {
+                while (L.pref[q + 1] <= f) ++q;
+                cols[u] = __ldg(P.csr_cols + L.ptr0[q] + (f - L.pref[q]));
+            }
+        }
+        fn(cols);
+    }
+}
+
+// Exact score of queued columns (their rows loaded from the CSC first),
+// lane-parallel over the CTA; accepted pairs applied as in the stream.
+template <int DMAX>
+__device__ __forceinline__ void score_queue_cols(const EngineArgs &a, const ProblemDev &P,
+                                                 const int32_t *queue, int qn,
+                                                 unsigned long long *acc_smem, bool ok,
+                                                 bool exact, unsigned long long *xmax_s,
+                                                 int spos) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int b0 = warp * 32; b0 < qn; b0 += blockDim.x) {
+        const int idx = b0 + lane;
+        bool acc = false;
+        if (ok && idx < qn) {
+            const int j = queue[idx * (DMAX + 1)];
+            int32_t rows[DMAX];
+#pragma unroll
+            for (int t = 0; t < DMAX; ++t)
+                rows[t] = (t < P.d) ? __ldg(P.csc_rows + (size_t)j * P.d + t) : 0;
+            acc = score_inline<DMAX, false, true>(a, P, j, rows, exact, xmax_s, spos);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, acc);
+        if (lane == 0 && bal) atomicAdd(acc_smem, (unsigned long long)__popc(bal));
+    }
+}
+
+// Out of line (its registers do not add to the column stream's); returns
+// the launch's ok flag, and the caller advances the fingerprint sequence.
+template <int DMAX, int THREADS>
+__device__ __noinline__ bool score_rows(const EngineArgs &a, const ProblemDev &P, int seg_lo,
+                                        int seg_hi, int g, int it, int rmode, ScoreSmem S,
+                                        unsigned fp_seq, bool ok, Prefetch *pf, int *s_R,
+                                        int *s_E) {
+    const bool exact = rmode == 0;
+    const int spos = a.shifted ? it % P.d : -1;
+    const int T = (a.mode == CCS_SCORE_COUNT) ? a.alpha : (a.alpha + P.d + 1) / 2;
+    unsigned long long *acc_slot = &P.ctrl->acc[g & 3];
+    const RowList L = row_list(a, S);
+    const int cap = (int)(((long long)a.stages * a.stage_bytes - 16) / 16);
+
+    __syncthreads();  // previous users of the queue and fingerprints are done
+    if (threadIdx.x == 0) {
+        *S.qn = 0;
+        *S.acc = 0;
+        *S.xmax = 0;
+    }
+    if (rmode == 2) enter_segment_slots<DMAX>(P, seg_lo, seg_hi);
+    __syncthreads();
+    if (threadIdx.x == 0 && ok && !(pf && pf->fp)) {
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        const uint32_t total = (uint32_t)align_up((size_t)P.m * (fp16_for(P.m) ? 2 : 1), 16);
+        mbar_expect_tx(S.fp_bar, total);
+        for (uint32_t off = 0; off < total; off += kFpChunk)
+            bulk_g2s(S.fp + off, P.fp + off, min((uint32_t)kFpChunk, total - off), S.fp_bar);
+    }
+    ok = ok && mbar_wait(a, S.fp_bar, fp_seq & 1u);
+    if (pf && threadIdx.x == 0) pf->fp = false;
+    if (!__syncthreads_and(ok)) return false;
+    if (a.stamps && blockIdx.x == 0 && threadIdx.x == 0 && g < kMaxStampIters)
+        a.stamps[kSubBase + 3 * g] = globaltimer();
+
+    int E = 0;
+    const int R = fp16_for(P.m) ? list_nonzero_rows<THREADS, true>(P, S.fp, L, cap, &E)
+                                : list_nonzero_rows<THREADS, false>(P, S.fp, L, cap, &E);
+    if (threadIdx.x == 0) {
+        *s_R = R;
+        *s_E = E;
+    }
+    // count each column's nonzero rows; a column reaching T is a candidate
+    unsigned n_inline = 0;
+    for_my_row_entries<THREADS>(P, L, R, E, [&](const int (&cols)[kRowUnroll]) {
+        unsigned old[kRowUnroll];
+#pragma unroll
+        for (int u = 0; u < kRowUnroll; ++u)
+            old[u] = cols[u] >= 0 ? atomicAdd(P.hits + (cols[u] >> 2), 1u << ((cols[u] & 3) * 8))
+                                  : 0u;
+#pragma unroll
+        for (int u = 0; u < kRowUnroll; ++u) {
+            if (cols[u] < 0) continue;
+            const unsigned c = (old[u] >> ((cols[u] & 3) * 8)) & 0xffu;
+            if (c + 1u != (unsigned)T) continue;
+            const int q = (a.debug_flags & kFlagRowInline) ? a.queue_cap : atomicAdd(S.qn, 1);
+            if (q < a.queue_cap) {
+                S.queue[q * (DMAX + 1)] = cols[u];
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(P.csc_rows + (size_t)cols[u] * P.d));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(P.x_hat + cols[u]));
+            } else {  // queue full: score it here
+                int32_t rows[DMAX];
+#pragma unroll
+                for (int t = 0; t < DMAX; ++t)
+                    rows[t] = (t < P.d) ? __ldg(P.csc_rows + (size_t)cols[u] * P.d + t) : 0;
+                n_inline += score_inline<DMAX, false, true>(a, P, cols[u], rows, exact, S.xmax,
+                                                            spos);
+            }
+        }
+    });
+    if (n_inline) atomicAdd(S.acc, (unsigned long long)n_inline);
+    __syncthreads();  // counting done, queue complete
+    if (a.stamps && blockIdx.x == 0 && threadIdx.x == 0 && g < kMaxStampIters)
+        a.stamps[kSubBase + 3 * g + 1] = globaltimer();
+    score_queue_cols<DMAX>(a, P, S.queue, min(*S.qn, a.queue_cap), S.acc, ok, exact, S.xmax,
+                           spos);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (*S.acc) atomicAdd(acc_slot, *S.acc);
+        if (exact && *S.xmax) atomicMax(&P.ctrl->xmax[(it + 1) & 1], *S.xmax);
+        if (blockIdx.x == 0) {
+            P.ctrl->row_driven += 1;
+            P.ctrl->row_entries += E;
+        }
+        if (a.stamps && blockIdx.x == 0 && g < kMaxStampIters)
+            a.stamps[kSubBase + 3 * g + 2] = globaltimer();
+    }
+    return ok;
+}
+
+// After a row-driven score phase (its counting done on every CTA): every
+// counter back to zero.  A coalesced sweep over this CTA's share of the
+// n / 4 words (16 bytes a thread and step) costs less than clearing the
+// counted words one by one: those are scattered, n / 4 words are few.
+template <int THREADS>
+__device__ __noinline__ void row_hits_clear(const ProblemDev &P) {
+    const long long nw = (P.n + 3) / 4, nq = nw / 4;  // words, whole 16-byte groups
+    const long long q0 = nq * blockIdx.x / gridDim.x, q1 = nq * (blockIdx.x + 1) / gridDim.x;
+    uint4 *h4 = reinterpret_cast<uint4 *>(P.hits);  // 256-byte aligned in the workspace
+    for (long long q = q0 + threadIdx.x; q < q1; q += THREADS) h4[q] = make_uint4(0u, 0u, 0u, 0u);
+    if (blockIdx.x == gridDim.x - 1)
+        for (long long w = nq * 4 + threadIdx.x; w < nw; w += THREADS) P.hits[w] = 0u;
 }
 
 // ---- exactness certificate of the incremental residual --------------------
@@ -974,6 +1311,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
     __shared__ int s_gridb, s_deg;
     __shared__ int s_ovf_n;
     __shared__ int s_ovf[kOvfCap];  // rows whose sum needs the whole CSR row
+    __shared__ int s_rows_R, s_rows_E, s_rowmode;  // the iteration's row-driven phase
     __shared__ int s_wbuf[(kWarps - 1) * kWbufPerWarp];
     ScoreSmem S;
     S.fp = smem;
@@ -1034,7 +1372,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
         my_tiles(t0, t1);
         if (t1 <= t0) return;
         if (a.single.flags & kPdUseFp) prefetch_fp(a.single, S, pf);
-        prefetch_chunks(a, a.single, t0, t1, kPer, S, chunk_seq, pf, ok);
+        // a row-driven iteration streams no CSC (its row list uses the ring)
+        if (!row_driven_iter(a, a.single, s_base[0] + g_next, __ldcg(&a.single.ctrl->r0)))
+            prefetch_chunks(a, a.single, t0, t1, kPer, S, chunk_seq, pf, ok);
     };
     if (threadIdx.x == 0) {
         pf.chunks = 0;
@@ -1048,13 +1388,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
     // ---- init: x_hat <- 0, r <- y (Alg. 2, first line) --------------------
     if (!a.probs) {
         // one problem: grid-stride over its columns and rows
+        // (the in-slots flags are set when the ordered residual begins)
         const ProblemDev &P = a.single;
         const long long gtid = blockIdx.x * (long long)THREADS + threadIdx.x;
         const long long gstride = (long long)gridDim.x * THREADS;
-        for (long long j = gtid; j < P.n; j += gstride) {
-            P.x_hat[j] = 0.0;
-            P.in_slots[j] = 0;
-        }
+        for (long long j = gtid; j < P.n; j += gstride) P.x_hat[j] = 0.0;
+        for (long long w = gtid; w < (P.n + 3) / 4; w += gstride) P.hits[w] = 0u;
         init_stats_begin(s_sum, s_umax, s_gridb, s_deg);
         InitStats st;
         for (long long i = gtid; i < P.m; i += gstride) init_row(P, (int)i, st);
@@ -1138,8 +1477,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
         if (!a.probs) {
             int t0, t1;
             my_tiles(t0, t1);
-            if (t1 > t0)
-                score_segment<DMAX, THREADS>(a, a.single, t0, t1, g, s_base[0] + g, s_rmode[0], S,
+            const int it = s_base[0] + g;
+            const bool rows_mode = row_driven_iter(a, a.single, it, __ldcg(&a.single.ctrl->r0));
+            if (threadIdx.x == 0) s_rowmode = rows_mode;
+            if (rows_mode) {
+                ok = score_rows<DMAX, THREADS>(a, a.single, t0, t1, g, it, s_rmode[0], S, fp_seq,
+                                               ok, &pf, &s_rows_R, &s_rows_E);
+                ++fp_seq;
+            } else if (t1 > t0)
+                score_segment<DMAX, THREADS>(a, a.single, t0, t1, g, it, s_rmode[0], S,
                                              chunk_seq, fp_seq, ok, &pf);
         } else {
             build_partition<THREADS>(a, s_status, s_pref, kPartScore);
@@ -1219,6 +1565,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
             const long long tiles = (a.single.m + kTile - 1) / kTile;
             residual_segment(0, a.single, (int)(tiles * blockIdx.x / gridDim.x),
                              (int)(tiles * (blockIdx.x + 1) / gridDim.x));
+            __syncthreads();
+            if (s_rowmode) row_hits_clear<THREADS>(a.single);
         } else {
             build_partition<THREADS>(a, s_status, s_pref, kPartRows);
             for_my_segments(a, s_status, s_pref, kPartRows,
@@ -1273,7 +1621,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
             res.iterations = P.ctrl->iteration;
             res.r0_final = __ldcg(&P.ctrl->r0);
             res.error = __ldcg(&a.sync->error) ? CCS_ETIMEOUT : CCS_OK;
-            res.reserved = 0;
+            res.row_driven = P.ctrl->row_driven;
+            res.row_entries = P.ctrl->row_entries;
             a.dev_out[P.out_slot] = res;
         }
     }

@@ -46,7 +46,8 @@ struct alignas(64) DecodeCtrl {
     int ordered;                // 1 once the problem runs the ordered residual
     int empty_run[2];           // iterations in a row that accepted nothing, before
                                 // iteration t (slot t & 1; persistent engine)
-    int pad[3];
+    int row_driven;             // iterations whose score phase went row-driven
+    long long row_entries;      // CSR entries those score phases read
 };
 static_assert(sizeof(DecodeCtrl) == 128, "DecodeCtrl layout");
 
@@ -74,6 +75,9 @@ struct ProblemDev {
                           // those columns, unordered
     uint8_t *fp;          // m fingerprints of r_i (0 iff r_i == 0): 16-bit when
                           // fp16_for(m), else 8-bit
+    uint32_t *hits;       // ceil(n/4) words, one byte per column: the nonzero rows
+                          // a row-driven score phase counted for the column
+                          // (zero between phases; persistent engine, one problem)
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -102,7 +106,9 @@ __host__ inline size_t decode_ws_layout(int n, int m, ProblemDev *pd, char *base
     char *slots = take((size_t)m * kSlotRec * 4);
     char *fp = take(fp_bytes(m));
     char *r_next = take((size_t)m * 8);
+    char *hits = take(align_up((size_t)n, 4));
     if (pd) {
+        pd->hits = reinterpret_cast<uint32_t *>(hits);
         pd->r_next = reinterpret_cast<double *>(r_next);
         pd->fp = reinterpret_cast<uint8_t *>(fp);
         pd->touched = reinterpret_cast<uint8_t *>(touched);
@@ -195,6 +201,14 @@ size_t engine_resume_header_bytes(int P);
 // descriptors after those of the groups before it.
 int engine_capture(ProblemDev *pds, const int *sizes, int groups, const ccs_params &prm, char *ws,
                    ccs_result *dev_out, cudaGraphExec_t *exec);
+// The expander's construction in two enqueued parts (ccs_setup.cu), for
+// callers that batch the read-back of the largest row degree.
+int expander_build_async(int32_t n, int32_t m, int32_t d, uint64_t seed, int32_t *csc_rows,
+                         int64_t *csr_ptr, int32_t *csr_cols, void *ws, cudaStream_t s,
+                         int **max_deg_dev);
+int expander_sort_rows(int32_t m, int64_t *csr_ptr, int32_t *csr_cols, int host_max,
+                       cudaStream_t s);
+
 int engine_resume(ProblemDev *pds, int P, const ccs_params &prm, int iter_budget, ccs_result *out,
                   char *hdr, cudaStream_t s);
 // A multi-group batch with merged tails (see ccs_engine.cu), run now or

@@ -15,6 +15,17 @@
 // each admitted request's state from it (first fit, 256-byte aligned) and the
 // launch header once.  A request whose state can never fit is refused at
 // submission (CCS_EBUDGET); one that does not fit now waits in the queue.
+//
+// Two kinds of request:
+//  - device requests (ccs_server_submit): A, y and the outputs are caller
+//    device arrays; the pool holds the decode state only;
+//  - seeded requests (ccs_server_submit_seeded): the pool holds everything
+//    the request keeps on the device -- A (CSC and CSR, drawn on the device
+//    from the request's seed at admission), y (copied from the host at
+//    admission), x_hat, r, the decode state -- so the pool bounds the HBM
+//    the server uses.  When the request finishes, x_hat (and r, the ||r||_0
+//    history if asked for) are copied to the caller's host buffers, and
+//    only then is its memory returned to the pool and its result published.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -82,7 +93,11 @@ class PoolAllocator {
 
 struct Request {
     int64_t ticket;
-    ccs_problem prob;
+    ccs_problem prob;     // device arrays (for a seeded request: pool memory,
+                          // filled in at admission)
+    bool seeded = false;
+    bool prepared = false;   // seeded: A drawn and y uploaded
+    ccs_seeded_request host{};  // seeded: the caller's host buffers
     size_t state_bytes = 0, off = 0;
     bool fresh = true;
     int rounds = 0;
@@ -107,6 +122,7 @@ struct ccs_server {
     std::vector<ccs::Request> inflight;
     std::unordered_map<int64_t, ccs::Request> finished;
     int64_t next_ticket = 1;
+    int *host_max = nullptr;  // pinned: largest row degree per seeded request being prepared
     bool stop = false;
     int error = CCS_OK;
     ccs_server_stats stats{};
@@ -117,6 +133,106 @@ namespace ccs {
 
 static size_t request_state_bytes(int32_t n, int32_t m) {
     return align_up(sizeof(DecodeCtrl), 256) + decode_ws_layout(n, m, nullptr, nullptr);
+}
+
+// Pool layout of a seeded request after its decode state: CSC, CSR offsets,
+// CSR columns, y, x_hat, r, the ||r||_0 history and the expander's
+// generation workspace.  Returns the total bytes; with base != null fills
+// the request's device pointers (and *gen_ws).
+static size_t seeded_layout(int32_t n, int32_t m, int32_t d, int32_t max_iter, char *base,
+                            ccs_problem *prob, char **gen_ws, size_t *gen_bytes) {
+    size_t off = align_up(request_state_bytes(n, m), 256);
+    auto take = [&](size_t bytes) {
+        char *p = base ? base + off : nullptr;
+        off = align_up(off + bytes, 256);
+        return p;
+    };
+    char *csc = take((size_t)n * d * 4);
+    char *ptr = take(((size_t)m + 1) * 8);
+    char *cols = take((size_t)n * d * 4);
+    char *y = take((size_t)m * 8);
+    char *x = take((size_t)n * 8);
+    char *r = take((size_t)m * 8);
+    char *hist = take(((size_t)max_iter + 1) * 8);
+    const size_t gb = ccs_workspace_size(CCS_OP_MAKE_EXPANDER, n, m, d);
+    char *gw = take(gb);
+    if (base) {
+        prob->csc_rows = reinterpret_cast<const int32_t *>(csc);
+        prob->csr_ptr = reinterpret_cast<const int64_t *>(ptr);
+        prob->csr_cols = reinterpret_cast<const int32_t *>(cols);
+        prob->y = reinterpret_cast<const double *>(y);
+        prob->x_hat = reinterpret_cast<double *>(x);
+        prob->r = reinterpret_cast<double *>(r);
+        prob->r0_hist = reinterpret_cast<int64_t *>(hist);
+        *gen_ws = gw;
+        *gen_bytes = gb;
+    }
+    return off;
+}
+
+// Seeded requests just admitted (indices `todo` of inflight): upload each y,
+// draw each A from its seed into the pool -- every request's construction
+// enqueued first, then one wait for all their largest row degrees, then the
+// row sorts -- so the worker waits on the stream once per admission, not
+// once per request.  rcs[q] receives each request's status.
+static void prepare_seeded(ccs_server *S, const std::vector<int> &todo, std::vector<int> &rcs) {
+    const int Q = (int)todo.size();
+    rcs.assign(Q, CCS_OK);
+    std::vector<char *> gen(Q, nullptr);
+    std::vector<int *> maxdev(Q, nullptr);
+    // y first: a copy from pageable memory waits for the stream, which is
+    // idle now and would not be once the constructions are enqueued
+    for (int q = 0; q < Q; ++q) {
+        Request &R = S->inflight[todo[q]];
+        const ccs_seeded_request &h = R.host;
+        size_t gen_bytes = 0;
+        seeded_layout(h.n, h.m, h.d, S->cfg.params.max_iter, S->pool + R.off, &R.prob, &gen[q],
+                      &gen_bytes);
+        if (cudaMemcpyAsync(const_cast<double *>(R.prob.y), h.y, (size_t)h.m * 8,
+                            cudaMemcpyHostToDevice, S->stream) != cudaSuccess)
+            rcs[q] = cuda_fail(cudaGetLastError(), "server: upload of y");
+    }
+    for (int q = 0; q < Q; ++q) {
+        if (rcs[q]) continue;
+        Request &R = S->inflight[todo[q]];
+        const ccs_seeded_request &h = R.host;
+        rcs[q] = expander_build_async(h.n, h.m, h.d, h.a_seed,
+                                      const_cast<int32_t *>(R.prob.csc_rows),
+                                      const_cast<int64_t *>(R.prob.csr_ptr),
+                                      const_cast<int32_t *>(R.prob.csr_cols), gen[q], S->stream,
+                                      &maxdev[q]);
+        if (!rcs[q] && cudaMemcpyAsync(S->host_max + q, maxdev[q], sizeof(int),
+                                       cudaMemcpyDeviceToHost, S->stream) != cudaSuccess)
+            rcs[q] = cuda_fail(cudaGetLastError(), "server: read-back of the row degrees");
+    }
+    if (cudaStreamSynchronize(S->stream) != cudaSuccess) {
+        const int rc = cuda_fail(cudaGetLastError(), "server: constructing A");
+        for (int q = 0; q < Q; ++q) rcs[q] = rcs[q] ? rcs[q] : rc;
+        return;
+    }
+    for (int q = 0; q < Q; ++q) {
+        if (rcs[q]) continue;
+        Request &R = S->inflight[todo[q]];
+        rcs[q] = expander_sort_rows(R.host.m, const_cast<int64_t *>(R.prob.csr_ptr),
+                                    const_cast<int32_t *>(R.prob.csr_cols), S->host_max[q],
+                                    S->stream);
+        if (!rcs[q]) R.prepared = true;
+    }
+}
+
+// Seeded request finished: its outputs to the caller's host buffers.
+static int deliver_seeded(ccs_server *S, const Request &R) {
+    const ccs_seeded_request &h = R.host;
+    cudaError_t e = cudaMemcpyAsync(h.x_hat, R.prob.x_hat, (size_t)h.n * 8,
+                                    cudaMemcpyDeviceToHost, S->stream);
+    if (e == cudaSuccess && h.r)
+        e = cudaMemcpyAsync(h.r, R.prob.r, (size_t)h.m * 8, cudaMemcpyDeviceToHost, S->stream);
+    if (e == cudaSuccess && h.r0_hist)
+        e = cudaMemcpyAsync(h.r0_hist, R.prob.r0_hist,
+                            ((size_t)R.result.iterations + 1) * 8, cudaMemcpyDeviceToHost,
+                            S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    return e == cudaSuccess ? CCS_OK : cuda_fail(e, "server: copy of the results to the host");
 }
 
 static void worker_loop(ccs_server *S) {
@@ -151,6 +267,35 @@ static void worker_loop(ccs_server *S) {
             if ((int64_t)S->inflight.size() > S->stats.peak_inflight)
                 S->stats.peak_inflight = (int64_t)S->inflight.size();
         }
+        // seeded requests admitted just now: A drawn from the seed, y uploaded.
+        // One that fails finishes with its error and leaves the round.
+        {
+            std::vector<int> todo, rcs;
+            for (size_t q = 0; q < S->inflight.size(); ++q)
+                if (S->inflight[q].seeded && !S->inflight[q].prepared) todo.push_back((int)q);
+            if (!todo.empty()) prepare_seeded(S, todo, rcs);
+            std::vector<Request> failed;
+            for (int q = (int)todo.size() - 1; q >= 0; --q) {
+                if (rcs[q] == CCS_OK) continue;
+                Request &R = S->inflight[todo[q]];
+                R.result = ccs_result{};
+                R.result.error = rcs[q];
+                failed.push_back(R);
+                S->inflight.erase(S->inflight.begin() + todo[q]);
+            }
+            if (!failed.empty()) {
+                std::lock_guard<std::mutex> lk(S->mu);
+                const double t = now_s();
+                for (Request &R : failed) {
+                    R.done_s = t;
+                    S->alloc->release(R.off, R.state_bytes);
+                    S->finished[R.ticket] = R;
+                    S->stats.completed += 1;
+                }
+                S->cv_done.notify_all();
+                if (S->inflight.empty()) continue;
+            }
+        }
         // build this round's problem list (the worker alone touches inflight
         // entries' device state; submitters only append to `pending`)
         const int P = (int)S->inflight.size();
@@ -180,6 +325,17 @@ static void worker_loop(ccs_server *S) {
         if (rc == CCS_OK)
             rc = engine_resume(pds.data(), P, S->cfg.params, S->cfg.iters_per_round, res.data(),
                                S->pool + S->header_off, S->stream);
+        // finished seeded requests hand their outputs to the host before their
+        // memory returns to the pool (outside the lock: it waits on the stream)
+        std::vector<int> deliver_rc(P, CCS_OK);
+        for (int p = 0; p < P; ++p) {
+            Request &R = S->inflight[p];
+            const bool done = rc != CCS_OK || res[p].status != kRunning || res[p].error;
+            if (done && R.seeded && rc == CCS_OK) {
+                R.result = res[p];
+                deliver_rc[p] = deliver_seeded(S, R);
+            }
+        }
         {
             std::lock_guard<std::mutex> lk(S->mu);
             S->stats.rounds += 1;
@@ -194,6 +350,7 @@ static void worker_loop(ccs_server *S) {
                 if (done) {
                     R.result = res[p];
                     if (rc != CCS_OK) R.result.error = rc;
+                    else if (deliver_rc[p] != CCS_OK) R.result.error = deliver_rc[p];
                     R.done_s = t;
                     S->alloc->release(R.off, R.state_bytes);
                     S->finished[R.ticket] = R;
@@ -242,6 +399,12 @@ extern "C" int ccs_server_create(const ccs_server_config *cfg, ccs_stream_t stre
     // pool_bytes is (its sync word and descriptors are accessed atomically)
     S->header_off = (cfg->pool_bytes - hdr) & ~(size_t)255;
     S->alloc = new PoolAllocator(S->header_off);
+    if (cudaHostAlloc(reinterpret_cast<void **>(&S->host_max), sizeof(int) * cfg->max_batch,
+                      cudaHostAllocDefault) != cudaSuccess) {
+        delete S->alloc;
+        delete S;
+        return cuda_fail(cudaGetLastError(), "ccs_server_create: pinned host buffer");
+    }
     S->worker = std::thread(worker_loop, S);
     *out = S;
     return CCS_OK;
@@ -274,6 +437,53 @@ extern "C" int ccs_server_submit(ccs_server *S, const ccs_problem *req, int64_t 
         std::lock_guard<std::mutex> lk(S->mu);
         if (S->stop) {
             set_last_error("ccs_server_submit: server is shutting down");
+            return CCS_EBUSY;
+        }
+        R.ticket = S->next_ticket++;
+        R.submit_s = now_s();
+        S->pending.push_back(R);
+        S->stats.submitted += 1;
+        *ticket = R.ticket;
+    }
+    S->cv_work.notify_one();
+    return CCS_OK;
+}
+
+extern "C" size_t ccs_seeded_request_bytes(int32_t n, int32_t m, int32_t d, int32_t max_iter) {
+    if (check_sizes(n, m, d) != CCS_OK || max_iter < 0) return 0;
+    return seeded_layout(n, m, d, max_iter, nullptr, nullptr, nullptr, nullptr);
+}
+
+extern "C" int ccs_server_submit_seeded(ccs_server *S, const ccs_seeded_request *req,
+                                        int64_t *ticket) {
+    if (!S || !req || !ticket) {
+        set_last_error("ccs_server_submit_seeded: null argument");
+        return CCS_EINVAL;
+    }
+    int rc = check_sizes(req->n, req->m, req->d);
+    if (rc) return rc;
+    if ((rc = check_params(&S->cfg.params, req->d))) return rc;
+    if (!req->y || !req->x_hat) {
+        set_last_error("ccs_server_submit_seeded: null y or x_hat");
+        return CCS_EINVAL;
+    }
+    Request R;
+    R.seeded = true;
+    R.host = *req;
+    R.prob.n = req->n;
+    R.prob.m = req->m;
+    R.prob.d = req->d;
+    R.state_bytes = seeded_layout(req->n, req->m, req->d, S->cfg.params.max_iter, nullptr,
+                                  nullptr, nullptr, nullptr);
+    if (R.state_bytes > S->alloc->size()) {
+        set_last_error("ccs_server_submit_seeded: request needs %zu bytes, pool holds %zu",
+                       R.state_bytes, S->alloc->size());
+        return CCS_EBUDGET;
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop) {
+            set_last_error("ccs_server_submit_seeded: server is shutting down");
             return CCS_EBUSY;
         }
         R.ticket = S->next_ticket++;
@@ -348,6 +558,7 @@ extern "C" int ccs_server_destroy(ccs_server *S) {
     S->cv_work.notify_all();
     if (S->worker.joinable()) S->worker.join();
     const int err = S->error;
+    cudaFreeHost(S->host_max);
     delete S->alloc;
     delete S;
     return err;

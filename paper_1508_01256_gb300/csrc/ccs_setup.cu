@@ -391,25 +391,17 @@ size_t ccs_workspace_size(int32_t op, int32_t n, int32_t m, int32_t d) {
     return 0;
 }
 
-int ccs_make_expander(int32_t n, int32_t m, int32_t d, uint64_t seed, int32_t *csc_rows,
-                      int64_t *csr_ptr, int32_t *csr_cols, void *ws, size_t ws_bytes,
-                      ccs_stream_t stream) {
-    int rc = check_sizes(n, m, d);
-    if (rc) return rc;
-    if (!csc_rows || !csr_ptr || !csr_cols || !ws) {
-        set_last_error("ccs_make_expander: null pointer argument");
-        return CCS_EINVAL;
-    }
-    if (ws_bytes < make_expander_ws(n, m)) {
-        set_last_error("ccs_make_expander: workspace %zu < %zu bytes", ws_bytes,
-                       make_expander_ws(n, m));
-        return CCS_ENOMEM;
-    }
-    if ((rc = check_problem_arrays("ccs_make_expander", csc_rows, csr_ptr, csr_cols, nullptr,
-                                   nullptr, nullptr, nullptr)) ||
-        (rc = check_aligned("ccs_make_expander", "ws", ws, kWorkspaceAlign)))
-        return rc;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace ccs {
+
+// First part of the expander's construction, all enqueued on `s`: the
+// columns, the row degrees and their prefix (csr_ptr), the CSR scatter.
+// *max_deg_dev receives the device address of the largest row degree, which
+// sizes the row sort (expander_sort_rows).  Arguments already checked.
+int expander_build_async(int32_t n, int32_t m, int32_t d, uint64_t seed, int32_t *csc_rows,
+                         int64_t *csr_ptr, int32_t *csr_cols, void *ws, cudaStream_t s,
+                         int **max_deg_dev) {
     char *base = static_cast<char *>(ws);
     int32_t *deg = reinterpret_cast<int32_t *>(base);
     const int nblocks = (m + kScanBlock - 1) / kScanBlock;
@@ -430,9 +422,15 @@ int ccs_make_expander(int32_t n, int32_t m, int32_t d, uint64_t seed, int32_t *c
     CCS_CUDA_TRY(cudaMemsetAsync(deg, 0, (size_t)m * 4, s));
     k_scatter_cols<<<grid_for(edges, 256), 256, 0, s>>>(n, d, csc_rows, csr_ptr, deg, csr_cols);
     CCS_CUDA_TRY(cudaGetLastError());
-    int host_max = 0;
-    CCS_CUDA_TRY(cudaMemcpyAsync(&host_max, max_deg, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CCS_CUDA_TRY(cudaStreamSynchronize(s));
+    *max_deg_dev = max_deg;
+    return CCS_OK;
+}
+
+// Second part: sort every CSR row ascending, given the largest row degree
+// (read back from expander_build_async).  CCS_EINVAL when a row is longer
+// than the on-chip sort takes.  Enqueued on `s`.
+int expander_sort_rows(int32_t m, int64_t *csr_ptr, int32_t *csr_cols, int host_max,
+                       cudaStream_t s) {
     if (host_max > kMaxSortRow) {
         set_last_error("ccs_make_expander: a row has %d columns (limit %d)", host_max,
                        kMaxSortRow);
@@ -451,6 +449,39 @@ int ccs_make_expander(int32_t n, int32_t m, int32_t d, uint64_t seed, int32_t *c
         k_sort_rows<<<grid, threads, smem, s>>>(m, cap, csr_ptr, csr_cols);
         CCS_CUDA_TRY(cudaGetLastError());
     }
+    return CCS_OK;
+}
+
+}  // namespace ccs
+
+extern "C" {
+
+int ccs_make_expander(int32_t n, int32_t m, int32_t d, uint64_t seed, int32_t *csc_rows,
+                      int64_t *csr_ptr, int32_t *csr_cols, void *ws, size_t ws_bytes,
+                      ccs_stream_t stream) {
+    int rc = check_sizes(n, m, d);
+    if (rc) return rc;
+    if (!csc_rows || !csr_ptr || !csr_cols || !ws) {
+        set_last_error("ccs_make_expander: null pointer argument");
+        return CCS_EINVAL;
+    }
+    if (ws_bytes < make_expander_ws(n, m)) {
+        set_last_error("ccs_make_expander: workspace %zu < %zu bytes", ws_bytes,
+                       make_expander_ws(n, m));
+        return CCS_ENOMEM;
+    }
+    if ((rc = check_problem_arrays("ccs_make_expander", csc_rows, csr_ptr, csr_cols, nullptr,
+                                   nullptr, nullptr, nullptr)) ||
+        (rc = check_aligned("ccs_make_expander", "ws", ws, kWorkspaceAlign)))
+        return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int *max_deg = nullptr;
+    if ((rc = expander_build_async(n, m, d, seed, csc_rows, csr_ptr, csr_cols, ws, s, &max_deg)))
+        return rc;
+    int host_max = 0;
+    CCS_CUDA_TRY(cudaMemcpyAsync(&host_max, max_deg, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CCS_CUDA_TRY(cudaStreamSynchronize(s));
+    if ((rc = expander_sort_rows(m, csr_ptr, csr_cols, host_max, s))) return rc;
     CCS_CUDA_TRY(cudaStreamSynchronize(s));
     return CCS_OK;
 }

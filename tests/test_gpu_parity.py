@@ -677,3 +677,85 @@ def test_scaled_pipeline_matches_oracle(ccs, orc, shape):
     assert np.array_equal(x.cpu().numpy(), orc.unscale(s_ref, ref["x_hat"]))
     if n >= 4096:
         assert g.status == ccs.CONVERGED and np.array_equal(x.cpu().numpy(), p.x)
+
+
+# ---- row-driven score phase ----------------------------------------------------
+#
+# Once ||r||_0 is small the engine finds the columns that can still be
+# accepted from the CSR rows of the nonzero r_i instead of streaming every
+# column.  Nothing may change: every decode below is compared bit for bit
+# with the oracle, with the phase taken as the engine chooses, forced
+# whenever its row list fits (bit 4), with its candidates scored one by one
+# (bit 3), and never (bit 5).
+
+ROW_ALWAYS, ROW_INLINE, ROW_NEVER = 16, 8, 32
+
+
+@pytest.mark.parametrize("case", ["extreme_2e22", "at_scale", "count", "shifted", "alpha3",
+                                  "ordered", "switch"])
+def test_row_driven_phase_matches_oracle(ccs, orc, case):
+    if case == "at_scale":
+        p = inputs.plain_at_scale(seed=41)
+    else:
+        p = inputs.extreme_undersampling(0.08, d=7, seed=42, log2n=22)
+    kw = dict(count=dict(score_mode=ccs.SCORE_COUNT, alpha=3),
+              shifted=dict(shifted=True), alpha3=dict(alpha=3),
+              ordered=dict(debug_flags=2), switch=dict(debug_flags=4)).get(case, {})
+    okw = {k: v for k, v in kw.items() if k != "debug_flags"}
+    if "score_mode" in okw:
+        okw["score_mode"] = orc.SCORE_COUNT
+    csc, ptr, cols, y = device_problem(ccs, p)
+    A, y_ref = oracle_problem(orc, p)
+    ref = orc.parallel_l0(A, p.m, y_ref, **okw)
+    seen_rows = False
+    for extra in (0, ROW_ALWAYS, ROW_ALWAYS | ROW_INLINE, ROW_NEVER):
+        flags = kw.get("debug_flags", 0) | extra
+        g = ccs.decode_parallel_l0(csc, ptr, cols, y, **dict(kw, debug_flags=flags))
+        assert_same_decode(g, ref)
+        if extra & ROW_NEVER:
+            assert g.row_driven == 0 and g.row_entries == 0
+        seen_rows |= g.row_driven > 0
+    assert seen_rows, "no decode took the row-driven phase"
+
+
+def test_row_driven_entries_count(ccs, orc):
+    """row_entries is the number of CSR entries of the nonzero rows summed
+    over the row-driven iterations: recomputed here from the oracle's
+    residuals, iteration by iteration, with the phase forced."""
+    p = inputs.extreme_undersampling(0.05, d=7, seed=43, log2n=22)
+    csc, ptr, cols, y = device_problem(ccs, p)
+    A, y_ref = oracle_problem(orc, p)
+    g = ccs.decode_parallel_l0(csc, ptr, cols, y, debug_flags=ROW_ALWAYS)
+    ref = orc.parallel_l0(A, p.m, y_ref, trace=True)
+    assert_same_decode(g, ref)
+    # a converged decode ran a score phase for exactly its traced iterations
+    assert ref["status"] == orc.CONVERGED and len(ref["trace"]) == ref["iterations"]
+    deg = np.diff(orc.transpose(A, p.m)[0])
+    x_hat = np.zeros(p.n)
+    want, iters = 0, 0
+    for it, idx, om in ref["trace"]:
+        r = orc.residual(A, p.m, y_ref, x_hat)
+        if it >= 1:  # the first iteration always streams the columns
+            want += int(deg[r != 0.0].sum())
+            iters += 1
+        x_hat[idx] = x_hat[idx] + om
+    assert g.row_driven == iters and g.row_entries == want
+
+
+@pytest.mark.parametrize("m", [4195, 4197, 40001, 40003])
+def test_row_driven_after_dirty_workspace(ccs, orc, m):
+    """The per-column counters live in the workspace: garbage there, and a
+    second decode on the same workspace, change nothing.  m is odd, so the
+    last word of the fingerprints (16-bit up to m = 32768, 8-bit above)
+    holds padding that the nonzero-row listing must skip."""
+    import torch
+    p = inputs.make_problem(2 ** 22, m, 7, inputs.round_half_up(0.05 * m), 44)
+    csc, ptr, cols, y = device_problem(ccs, p)
+    ws = ccs.workspace(ccs.ccs_workspace_size(ccs.OP_DECODE, p.n, p.m, p.d))
+    ws.fill_(0x5A)
+    A, y_ref = oracle_problem(orc, p)
+    ref = orc.parallel_l0(A, p.m, y_ref)
+    for _ in range(2):
+        g = ccs.decode_parallel_l0(csc, ptr, cols, y, ws=ws, debug_flags=ROW_ALWAYS)
+        assert_same_decode(g, ref)
+        assert g.row_driven >= 1

@@ -164,3 +164,73 @@ def test_serve_stream_ring_results_equal_alone(ccs):
     for s in range(R):
         a = alone[s % D]
         assert torch.equal(outs[s][0], a.x_hat) and torch.equal(outs[s][1], a.r)
+
+
+def _seeded_inputs(orc, shapes, seed):
+    """Host y of each (n, m, d, k) problem from the oracle's own expander and
+    measurement (the server draws the same A from the seed on the device)."""
+    out = []
+    for q, (n, m, d, k) in enumerate(shapes):
+        p = inputs.make_problem(n, m, d, k, seed + q)
+        A = orc.make_expander(n, m, d, p.a_seed)
+        out.append((p, A, orc.measure(A, m, p.x)))
+    return out
+
+
+def test_seeded_requests_equal_the_oracle(ccs, orc):
+    """Seeded requests (A drawn by the server into its pool, y from the host,
+    results copied back to the host) served in one mix with device requests:
+    every seeded result, x_hat, r and the ||r||_0 history, is bit-identical
+    to the oracle's decode of the same A and y; the device requests still
+    equal their decodes alone."""
+    shapes = [(4096, 410, 7, 41), (20000, 2000, 9, 400), (3000, 300, 7, 90),
+              (12000, 120, 7, 12), (8000, 2400, 9, 480), (5000, 500, 7, 150)]
+    seeded = _seeded_inputs(orc, shapes, 4100)
+    dev_probs = inputs.batch_problems(6, seed=23, log2n_hi=15.0, ds=(7, 9))
+    dev_reqs = _requests(ccs, dev_probs)
+    outs = [(np.full(p.n, np.nan), np.full(p.m, np.nan), np.full(101, -1, dtype=np.int64))
+            for p, _, _ in seeded]
+    with ccs.Server(512 << 20, max_batch=8, iters_per_round=2) as srv:
+        tickets = []
+        for (p, _, y), (xo, ro, ho), dq in zip(seeded, outs, dev_reqs):
+            tickets.append(srv.submit_seeded(p.n, p.m, p.d, p.a_seed, y, xo, ro, ho))
+            tickets.append(srv.submit(*dq))
+        infos = [srv.wait(t) for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == 12 and st["error"] == 0
+    for q, ((p, A, y), (xo, ro, ho)) in enumerate(zip(seeded, outs)):
+        res = infos[2 * q].result
+        ref = orc.parallel_l0(A, p.m, y)
+        assert res.error == 0
+        assert (res.status, res.iterations, res.r0_final) == \
+            (ref["status"], ref["iterations"], ref["r0_final"])
+        assert np.array_equal(xo.view(np.int64), ref["x_hat"].view(np.int64))
+        assert np.array_equal(ro.view(np.int64), ref["r"].view(np.int64))
+        assert ho[:res.iterations + 1].tolist() == list(ref["r0_hist"])
+    _check_same_as_alone(ccs, dev_reqs, infos[1::2])
+
+
+def test_seeded_admission_bounds_the_pool(ccs, orc):
+    """A pool that holds two seeded requests (A, y, outputs and state
+    included): the others wait; the pool's peak use stays within it; every
+    result equals the oracle's."""
+    shapes = [(60000, 6000, 7, 600)] * 5
+    seeded = _seeded_inputs(orc, shapes, 5200)
+    one = ccs.ccs_seeded_request_bytes(60000, 6000, 7, 100)
+    assert one > 2 * 60000 * 7 * 4  # CSC and CSR are part of it
+    pool = 2 * one + (1 << 20)
+    outs = [np.full(p.n, np.nan) for p, _, _ in seeded]
+    with ccs.Server(pool, max_batch=8, iters_per_round=1) as srv:
+        tickets = [srv.submit_seeded(p.n, p.m, p.d, p.a_seed, y, xo)
+                   for (p, _, y), xo in zip(seeded, outs)]
+        infos = [srv.wait(t) for t in tickets]
+        st = srv.stats()
+        with pytest.raises(ccs.CcsError) as ei:  # can never fit
+            srv.submit_seeded(600000, 60000, 7, 1, np.zeros(60000), np.zeros(600000))
+        assert ei.value.code == ccs.CCS_EBUDGET
+    assert st["peak_inflight"] <= 2 and st["peak_bytes"] <= pool - (1 << 20) + 256
+    assert max(i.admit_s for i in infos) > min(i.done_s for i in infos)
+    for (p, A, y), xo, info in zip(seeded, outs, infos):
+        ref = orc.parallel_l0(A, p.m, y)
+        assert info.result.status == ref["status"]
+        assert np.array_equal(xo, ref["x_hat"])
