@@ -114,16 +114,25 @@ typedef struct {
                              launch) steer the row-driven score phase: bit 3
                              scores its candidates one by one instead of
                              queueing them, bit 4 takes it whenever its row
-                             list fits instead of only once ||r||_0 <= m/32
+                             list fits instead of only once ||r||_0 <= m/64
                              on a CSC of at least 2^26 entries, bit 5 never
                              takes it.  Results are the same
                              for every setting of bits 1-5.                  */
-    int32_t schedule;     /* persistent-engine launch shape: 0 = library's
+    int32_t schedule;     /* persistent-engine launch shape, 0..127.
+                             Bits 0-1, the thread shape: 0 = library's
                              choice (1 when d <= 8, else 2); 1 = 1024
                              threads a CTA, one 32-column tile per warp and
                              chunk (d <= 8 only); 2 = 512 threads, two
                              tiles per warp and chunk; 3 = 768 threads, one
-                             tile per warp and chunk (d <= 8 only)          */
+                             tile per warp and chunk (d <= 8 only).
+                             Bits 2-4: the CSC stage ring's depth, 0 = as
+                             many stages as shared memory holds (at most
+                             6), else 2..6 at most.  Bits 5-6: the queue of
+                             candidate columns, 0 = as long as shared
+                             memory allows (at most 2048 a CTA), 1 = 256
+                             entries, 2 = 1024.  0 as a whole: the shape
+                             ccs_autotune recorded for this class of launch
+                             on this device, else the library's choice.   */
     int32_t shifted;      /* 0: Alg. 2, each column's candidate is the mode of
                              its nonzero residual values.  1: the shifted
                              variant of Sec. 4.3.1: at iteration l the only
@@ -141,7 +150,7 @@ typedef struct {
     int32_t error;        /* CCS_OK, or the CCS_E* code that ended this
                              problem early (e.g. CCS_ETIMEOUT)               */
     int32_t row_driven;   /* iterations whose score phase was row-driven:
-                             once ||r||_0 <= m/32 on a CSC too large for L2
+                             once ||r||_0 <= m/64 on a CSC too large for L2
                              (n d >= 2^26), the persistent engine (one
                              problem per launch) finds the columns that can
                              still be accepted from the CSR rows of the
@@ -314,8 +323,10 @@ CCS_API int ccs_decode_batch_async(const ccs_problem *probs, int32_t count,
  * or d > 8; fingerprints of r in shared memory or not).  ccs_autotune
  * decodes `probs` as ccs_decode_batch would, but runs each launch group with
  * every launch shape its kernel instances offer (CTAs of 1024, 768 or 512
- * threads for d <= 8; 512 for d > 8), twice each, timing the second run
- * with CUDA events on `stream`.  The fastest shape of each group is recorded
+ * threads for d <= 8; 512 for d > 8; each with the CSC ring at full depth or
+ * capped at 2 or 3 stages, and the candidate queue at full length or capped
+ * at 256 entries: 18 shapes for d <= 8, 6 above), twice each, timing the
+ * second run with CUDA events on `stream`.  The fastest shape of each group is recorded
  * in a table inside the library, per device and class (largest d of the
  * launch, fingerprint fit); from then on every launch on that device with
  * p->schedule == 0 in that class uses it.  tuned[0..3] receives the shape
@@ -326,6 +337,18 @@ CCS_API int ccs_decode_batch_async(const ccs_problem *probs, int32_t count,
 CCS_API int ccs_autotune(const ccs_problem *probs, int32_t count, const ccs_params *p,
                          void *ws, size_t ws_bytes, ccs_stream_t stream, int32_t *tuned);
 CCS_API void ccs_autotune_reset(void);
+/* The table's entry for the current device and a class (largest d of a
+ * launch, fingerprints of r in shared memory or not): the schedule code, 0
+ * when none is recorded. */
+CCS_API int ccs_autotune_get(int32_t dmax, int32_t fits, int32_t *schedule);
+/* The table on disk: ccs_autotune_save writes every recorded entry of every
+ * visible device, one line "gpu dmax fits schedule", the gpu keyed by
+ * model (name, SM count, compute capability); ccs_autotune_load installs
+ * the entries whose key matches a visible device, so a shape tuned once
+ * serves later processes on the same GPU model.  CCS_EINVAL when the file
+ * cannot be written or read; malformed lines are skipped. */
+CCS_API int ccs_autotune_save(const char *path);
+CCS_API int ccs_autotune_load(const char *path);
 
 /* ---- CUDA graph of a batched decode -----------------------------------------
  *

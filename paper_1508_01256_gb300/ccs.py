@@ -140,6 +140,12 @@ def lib() -> ctypes.CDLL:
         l.ccs_autotune.restype = ctypes.c_int
         l.ccs_autotune_reset.argtypes = []
         l.ccs_autotune_reset.restype = None
+        l.ccs_autotune_get.argtypes = [i32, i32, ctypes.POINTER(i32)]
+        l.ccs_autotune_get.restype = ctypes.c_int
+        l.ccs_autotune_save.argtypes = [ctypes.c_char_p]
+        l.ccs_autotune_save.restype = ctypes.c_int
+        l.ccs_autotune_load.argtypes = [ctypes.c_char_p]
+        l.ccs_autotune_load.restype = ctypes.c_int
         l.ccs_decode_parallel_l0_noalloc.argtypes = [i32, i32, i32, P, P, P, P, P, P, P,
                                                      ctypes.POINTER(Params),
                                                      ctypes.POINTER(Result), P]
@@ -347,6 +353,21 @@ def ccs_autotune(probs, p: Params | None, ws, stream=None) -> list:
 
 def ccs_autotune_reset() -> None:
     lib().ccs_autotune_reset()
+
+
+def ccs_autotune_get(dmax: int, fits: bool) -> int:
+    """The recorded launch shape of a class on the current device (0: none)."""
+    out = ctypes.c_int32()
+    _check(lib().ccs_autotune_get(dmax, int(fits), ctypes.byref(out)), "ccs_autotune_get")
+    return int(out.value)
+
+
+def ccs_autotune_save(path: str) -> None:
+    _check(lib().ccs_autotune_save(os.fsencode(path)), "ccs_autotune_save")
+
+
+def ccs_autotune_load(path: str) -> None:
+    _check(lib().ccs_autotune_load(os.fsencode(path)), "ccs_autotune_load")
 
 
 RESULT_BYTES = ctypes.sizeof(Result)

@@ -23,11 +23,15 @@ static size_t batch_ws(const ccs_problem *probs, int32_t count) {
     return engine_header_bytes(count) + engine_resume_header_bytes(count) + total;
 }
 
-// Time every launch shape the kernel instances offer for each launch group
-// (d <= 8: 1024, 768 and 512 threads; d > 8: 512 only) and record the
-// fastest for the group's class.  Each candidate decodes the group twice;
-// the second run is timed.  tuned[g] receives group g's choice (0..3 more
-// entries are set to 0).
+// Time every launch shape for each launch group and record the fastest for
+// the group's class.  The shapes: the thread shapes the kernel instances
+// offer (d <= 8: 1024, 768 and 512 threads; d > 8: 512 only), each with
+// the CSC ring as deep as shared memory allows or capped at 2 or 3 stages,
+// and the candidate queue as long as shared memory allows or capped at 256
+// entries (a shorter ring or queue leaves shared memory idle, but a deeper
+// one delays the first chunk's consumers and the queue's scoring round).
+// Each candidate decodes the group twice; the second run is timed.
+// tuned[g] receives group g's choice (0..3 more entries are set to 0).
 static int autotune_groups(std::vector<ProblemDev> &sub, const int *sizes, int groups,
                            const ccs_params &p, char *hdr, cudaStream_t s, int32_t *tuned) {
     int dev = 0;
@@ -45,9 +49,15 @@ static int autotune_groups(std::vector<ProblemDev> &sub, const int *sizes, int g
             dmax = std::max(dmax, sub[first + u].d);
             fits = fits && engine_fp_fits(sub[first + u], p);
         }
-        const int cands_small[3] = {1, 3, 2}, cands_large[1] = {2};
-        const int *cands = dmax <= 8 ? cands_small : cands_large;
-        const int ncand = dmax <= 8 ? 3 : 1;
+        const int shapes_small[3] = {1, 3, 2}, shapes_large[1] = {2};
+        const int *shapes = dmax <= 8 ? shapes_small : shapes_large;
+        const int nshape = dmax <= 8 ? 3 : 1;
+        const int stage_caps[3] = {0, 2, 3}, queue_codes[2] = {0, 1};
+        int cands[18];
+        int ncand = 0;
+        for (int t = 0; t < nshape; ++t)
+            for (int sc : stage_caps)
+                for (int qc : queue_codes) cands[ncand++] = shapes[t] | (sc << 2) | (qc << 5);
         int best = 0;
         float best_ms = 0.0f;
         for (int c = 0; c < ncand && rc == CCS_OK; ++c) {

@@ -176,8 +176,10 @@ int check_params(const ccs_params *p, int d) {
         set_last_error("unknown engine %d", p->engine);
         return CCS_EINVAL;
     }
-    if (p->watchdog_ms < 0 || p->schedule < 0 || p->schedule > 3) {
-        set_last_error("bad watchdog_ms or schedule");
+    const int stage_cap = (p->schedule >> 2) & 7;
+    if (p->watchdog_ms < 0 || p->schedule < 0 || p->schedule >= 128 || stage_cap == 1 ||
+        stage_cap > 6 || ((p->schedule >> 5) & 3) == 3) {
+        set_last_error("bad watchdog_ms or schedule (%d)", p->schedule);
         return CCS_EINVAL;
     }
     if (p->shifted != 0 && p->shifted != 1) {

@@ -3,6 +3,7 @@
 // launches, and resume-mode launches for the server.  The kernel itself is
 // in ccs_engine_kernel.cuh.
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <tuple>
@@ -16,14 +17,24 @@ namespace ccs {
 // Host side
 // ---------------------------------------------------------------------------
 
-// Schedules: (threads per CTA, tiles per consumer warp and chunk).
+// Launch shape (ccs_params.schedule): bits 0-1 the thread shape
+// (threads per CTA, tiles per consumer warp and chunk),
 //   1: 1024 threads, 1 tile  (d <= 8: at most 64 registers a thread)
 //   2:  512 threads, 2 tiles (any d: up to 128 registers a thread)
 //   3:  768 threads, 1 tile  (d <= 8: up to 85 registers a thread)
+// (0: the library's choice); bits 2-4 a cap on the CSC stages (0: as many
+// as shared memory holds, else 2..6); bits 5-6 a cap on the candidate
+// queue (0: as long as shared memory allows, 1: 256 entries, 2: 1024).
 static int schedule_for(int dmax, int requested) {
+    requested &= 3;
     if (requested == 2 || dmax > 8) return 2;
     if (requested == 3) return 3;
     return 1;  // measured fastest for d <= 8
+}
+static int stage_cap_of(int schedule) { return (schedule >> 2) & 7; }
+static int queue_cap_of(int schedule) {
+    const int q = (schedule >> 5) & 3;
+    return q == 1 ? 256 : (q == 2 ? 1024 : kQueueCap);
 }
 
 // Launch shapes picked by ccs_autotune, by device, largest d of a launch and
@@ -185,7 +196,7 @@ static int plan_launch(ProblemDev *pds, int P, const ccs_params &prm, LaunchPlan
         return CCS_EINVAL;
     }
     int requested = prm.schedule;
-    if (requested == 0) {
+    if ((requested & 3) == 0 && (requested >> 2) == 0) {
         // a shape picked by ccs_autotune for this class of launch, if any
         int dev = 0;
         CCS_CUDA_TRY(cudaGetDevice(&dev));
@@ -236,10 +247,11 @@ static int plan_launch(ProblemDev *pds, int P, const ccs_params &prm, LaunchPlan
         sched = 3;  // problems without fingerprints need the exact-path prefilter
         continue;
     }
-    const int stages =
-        (int)std::min<size_t>(kMaxStages, (smem_limit - fixed - fp_cap) / stage_bytes);
+    int stages = (int)std::min<size_t>(kMaxStages, (smem_limit - fixed - fp_cap) / stage_bytes);
+    if (stage_cap_of(requested) >= 2) stages = std::min(stages, stage_cap_of(requested));
     const size_t left = smem_limit - fp_cap - (size_t)stages * stage_bytes - status_bytes - 256;
-    const int queue_cap = (int)std::min<size_t>(kQueueCap, (left - 16) / entry);
+    const int queue_cap = (int)std::min<size_t>(
+        std::min(kQueueCap, queue_cap_of(requested)), (left - 16) / entry);
     const size_t smem = fp_cap + (size_t)stages * stage_bytes +
                         align_up((size_t)queue_cap * entry, 16) + status_bytes;
 
@@ -614,3 +626,81 @@ int engine_resume(ProblemDev *pds, int P, const ccs_params &prm, int iter_budget
 }  // namespace ccs
 
 extern "C" CCS_API void ccs_autotune_reset(void) { ccs::tuned_schedule_reset(); }
+
+namespace ccs {
+
+// The tuned table on disk is keyed by GPU: its name, SM count and compute
+// capability (one key per model, so a file written on one GB300 serves
+// every GB300).
+static bool gpu_key(int dev, char *out, size_t cap) {
+    cudaDeviceProp pr;
+    if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) return false;
+    size_t k = 0;
+    for (const char *c = pr.name; *c && k + 1 < cap; ++c) out[k++] = (*c == ' ') ? '_' : *c;
+    out[k] = 0;
+    std::snprintf(out + k, cap - k, "/sm%d/cc%d.%d", pr.multiProcessorCount, pr.major, pr.minor);
+    return true;
+}
+
+}  // namespace ccs
+
+extern "C" CCS_API int ccs_autotune_get(int32_t dmax, int32_t fits, int32_t *schedule) {
+    if (!schedule || dmax < 1 || dmax > ccs::kMaxD) {
+        ccs::set_last_error("ccs_autotune_get: bad arguments");
+        return CCS_EINVAL;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ccs::cuda_fail(cudaGetLastError(), "cudaGetDevice");
+    *schedule = ccs::tuned_schedule_get(dev, dmax, fits != 0);
+    return CCS_OK;
+}
+
+extern "C" CCS_API int ccs_autotune_save(const char *path) {
+    if (!path) return CCS_EINVAL;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) count = 0;
+    FILE *f = std::fopen(path, "w");
+    if (!f) {
+        ccs::set_last_error("ccs_autotune_save: cannot write %s", path);
+        return CCS_EINVAL;
+    }
+    std::fprintf(f, "# ccs launch shapes: gpu dmax fits schedule\n");
+    for (int dev = 0; dev < count && dev < 64; ++dev) {
+        char key[256];
+        if (!ccs::gpu_key(dev, key, sizeof key)) continue;
+        for (int dm = 1; dm <= ccs::kMaxD; ++dm)
+            for (int fits = 0; fits < 2; ++fits) {
+                const int sc = ccs::tuned_schedule_get(dev, dm, fits != 0);
+                if (sc) std::fprintf(f, "%s %d %d %d\n", key, dm, fits, sc);
+            }
+    }
+    const int bad = std::fclose(f);
+    return bad ? CCS_EINVAL : CCS_OK;
+}
+
+extern "C" CCS_API int ccs_autotune_load(const char *path) {
+    if (!path) return CCS_EINVAL;
+    FILE *f = std::fopen(path, "r");
+    if (!f) {
+        ccs::set_last_error("ccs_autotune_load: cannot read %s", path);
+        return CCS_EINVAL;
+    }
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) count = 0;
+    char line[512];
+    while (std::fgets(line, sizeof line, f)) {
+        char key[256];
+        int dm = 0, fits = 0, sc = 0;
+        if (line[0] == '#' || std::sscanf(line, "%255s %d %d %d", key, &dm, &fits, &sc) != 4)
+            continue;
+        if (dm < 1 || dm > ccs::kMaxD || (fits != 0 && fits != 1) || sc <= 0 || sc >= 128)
+            continue;
+        for (int dev = 0; dev < count && dev < 64; ++dev) {
+            char mine[256];
+            if (ccs::gpu_key(dev, mine, sizeof mine) && std::strcmp(mine, key) == 0)
+                ccs::tuned_schedule_set(dev, dm, fits != 0, sc);
+        }
+    }
+    std::fclose(f);
+    return CCS_OK;
+}

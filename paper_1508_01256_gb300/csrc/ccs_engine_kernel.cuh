@@ -59,7 +59,7 @@ constexpr int kFlagRowNever = 32;   // every score phase streams the CSC
 constexpr int kFpChunk = 32768;     // bytes per fingerprint bulk copy
 constexpr int kWbufPerWarp = 32;    // buffered candidate columns per consumer warp
 constexpr int kSubBase = 3 * kMaxStampIters + 2;  // CTA-0 score sub-phase stamps start here
-constexpr int kRowDrivenDiv = 32;   // row-driven score phase while ||r||_0 <= m / kRowDrivenDiv
+constexpr int kRowDrivenDiv = 64;   // row-driven score phase while ||r||_0 <= m / kRowDrivenDiv
 constexpr long long kRowDrivenMinEntries = 64ll << 20;  // ... and the CSC (n d entries) streams
                                                        // from HBM, not from L2
 constexpr int kRowUnroll = 16;      // CSR entries in flight per thread in that phase

@@ -229,6 +229,8 @@ def _main(argv=None):
     ph.add_argument("--d", type=int, nargs="+", default=[7])
     ph.add_argument("--per-point", type=int, default=10)
     ph.add_argument("--deltas", type=float, nargs="*", default=None)
+    ph.add_argument("--band", type=float, nargs="*", default=None,
+                    help="Sec. 5.6: banded signals with these fractions of equal values")
     ap.add_argument("--seed", type=int, default=20151508)
     args = ap.parse_args(argv)
     build.build()
@@ -241,9 +243,14 @@ def _main(argv=None):
             print(json.dumps(out), flush=True)
     else:
         for d in args.d:
-            for row in phase_transition(ccs, n=2 ** args.n_log2, d=d, deltas=args.deltas,
-                                        per_point=args.per_point, seed=args.seed, device=dev):
-                print(json.dumps(row), flush=True)
+            for band in (args.band or [None]):
+                kw = dict(model="banded", band=band) if band is not None else {}
+                for row in phase_transition(ccs, n=2 ** args.n_log2, d=d, deltas=args.deltas,
+                                            per_point=args.per_point, seed=args.seed, device=dev,
+                                            **kw):
+                    if band is not None:
+                        row["band"] = band
+                    print(json.dumps(row), flush=True)
 
 
 if __name__ == "__main__":

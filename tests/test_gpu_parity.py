@@ -602,11 +602,59 @@ def test_autotune_records_a_shape_and_keeps_results(ccs, orc):
         tuned = ccs.ccs_autotune(pbs, ccs.params(), ws)
         torch.cuda.synchronize()
         groups = [t for t in tuned if t]
-        assert len(groups) >= 2 and all(t in (1, 2, 3) for t in groups)
+        # thread shape 1..3, stage cap 0 or 2..3, queue cap 0..1
+        assert len(groups) >= 2 and all(
+            (t & 3) in (1, 2, 3) and (t >> 2) & 7 in (0, 2, 3) and (t >> 5) in (0, 1)
+            for t in groups)
         outs = ccs.decode_batch(items, history=True)
         for p, g in zip(probs, outs):
             A, y_ref = oracle_problem(orc, p)
             assert_same_decode(g, orc.parallel_l0(A, p.m, y_ref))
+    finally:
+        ccs.ccs_autotune_reset()
+
+
+@pytest.mark.parametrize("schedule", [1 | (2 << 2), 3 | (3 << 2) | (1 << 5), 2 | (6 << 2),
+                                      2 | (2 << 5), 1 | (1 << 5)])
+def test_explicit_launch_shapes_keep_results(ccs, orc, schedule):
+    """Stage and queue caps change the launch, never the decode: one problem
+    per d class, bit for bit against the oracle under each shape (d > 8 takes
+    the 512-thread instance whatever the thread shape asks)."""
+    for p in (inputs.make_problem(20000, 2000, 7, 400, 61),
+              inputs.make_problem(20000, 2000, 11, 300, 62)):
+        csc, ptr, cols, y = device_problem(ccs, p)
+        A, y_ref = oracle_problem(orc, p)
+        g = ccs.decode_parallel_l0(csc, ptr, cols, y, schedule=schedule)
+        assert_same_decode(g, orc.parallel_l0(A, p.m, y_ref))
+
+
+def test_autotune_table_round_trips_through_a_file(ccs, tmp_path):
+    """ccs_autotune_save / ccs_autotune_load: the recorded shapes come back
+    for this GPU model after a reset; lines for other GPUs or malformed ones
+    are ignored."""
+    import torch
+    probs = inputs.batch_problems(6, seed=58, log2n_hi=14.0, ds=(7,))
+    pbs, keep = [], []
+    for p in probs:
+        csc, ptr, cols, y = device_problem(ccs, p)
+        x_hat = torch.empty(p.n, dtype=torch.float64, device="cuda")
+        r = torch.empty(p.m, dtype=torch.float64, device="cuda")
+        keep.append((csc, ptr, cols, y, x_hat, r))
+        pbs.append(ccs.problem(csc, ptr, cols, y, x_hat, r))
+    ws = ccs.workspace(ccs.ccs_batch_workspace_size(pbs))
+    path = str(tmp_path / "shapes.txt")
+    try:
+        tuned = [t for t in ccs.ccs_autotune(pbs, ccs.params(), ws) if t]
+        assert tuned
+        want = ccs.ccs_autotune_get(7, True)
+        assert want == tuned[0]
+        ccs.ccs_autotune_save(path)
+        with open(path, "a") as f:
+            f.write("Some_Other_GPU/sm1/cc1.0 7 1 9\nnot a line\n")
+        ccs.ccs_autotune_reset()
+        assert ccs.ccs_autotune_get(7, True) == 0
+        ccs.ccs_autotune_load(path)
+        assert ccs.ccs_autotune_get(7, True) == want
     finally:
         ccs.ccs_autotune_reset()
 
