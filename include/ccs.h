@@ -116,8 +116,10 @@ typedef struct {
                              queueing them, bit 4 takes it whenever its row
                              list fits instead of only once ||r||_0 <= m/64
                              on a CSC of at least 2^26 entries, bit 5 never
-                             takes it.  Results are the same
-                             for every setting of bits 1-5.                  */
+                             takes it.  Bit 6: the column stream scores
+                             every candidate where it finds it instead of
+                             queueing it.  Results are the same for every
+                             setting of bits 1-6.                            */
     int32_t schedule;     /* persistent-engine launch shape, 0..127.
                              Bits 0-1, the thread shape: 0 = library's
                              choice (1 when d <= 8, else 2); 1 = 1024

@@ -56,8 +56,14 @@ constexpr int kFlagSwitch = 4;      // test hook: the certificate fails from ite
 constexpr int kFlagRowInline = 8;   // test hook: row-driven candidates scored inline, no queue
 constexpr int kFlagRowAlways = 16;  // test hook: row-driven whenever the row list fits
 constexpr int kFlagRowNever = 32;   // every score phase streams the CSC
+constexpr int kFlagStreamInline = 64;  // stream candidates scored where found, not queued
 constexpr int kFpChunk = 32768;     // bytes per fingerprint bulk copy
 constexpr int kWbufPerWarp = 32;    // buffered candidate columns per consumer warp
+// A buffered column's entry: its index, then its fingerprints packed two
+// (16-bit) or four (8-bit) to a word, so the buffer's test reads shared
+// memory only.
+template <int DMAX>
+constexpr int kWbufEntry = 1 + (DMAX + 1) / 2;
 constexpr int kSubBase = 3 * kMaxStampIters + 2;  // CTA-0 score sub-phase stamps start here
 constexpr int kRowDrivenDiv = 64;   // row-driven score phase while ||r||_0 <= m / kRowDrivenDiv
 constexpr long long kRowDrivenMinEntries = 64ll << 20;  // ... and the CSC (n d entries) streams
@@ -334,7 +340,8 @@ struct ScoreSmem {
     uint64_t *fp_bar;  // fingerprint copy
     int *qn;           // queue length
     unsigned long long *acc;  // accepted pairs of this CTA in the current segment
-    int *wbuf;         // per consumer warp: kWbufPerWarp buffered candidate columns
+    int *wbuf;         // per consumer warp: kWbufPerWarp buffered candidate columns,
+                       // kWbufEntry<DMAX> ints each
     unsigned long long *xmax;  // bits of the largest |x_hat_j| this CTA set (exact mode)
 };
 
@@ -516,7 +523,7 @@ __device__ __forceinline__ bool queue_or_score(const EngineArgs &a, const Proble
                                                int32_t *queue, int *qn, int j,
                                                const int32_t (&rows)[DMAX], bool exact,
                                                unsigned long long *xmax_s, int spos) {
-    const int q = atomicAdd(qn, 1);
+    const int q = (a.debug_flags & kFlagStreamInline) ? a.queue_cap : atomicAdd(qn, 1);
     if (q < a.queue_cap) {  // scored after the stream
         int32_t *e = queue + q * (DMAX + 1);
         e[0] = j;
@@ -529,31 +536,53 @@ __device__ __forceinline__ bool queue_or_score(const EngineArgs &a, const Proble
     return score_inline<DMAX, false, true>(a, P, j, rows, exact, xmax_s, spos);
 }
 
-// The fingerprint test, then queue (or inline exact score), of up to 32
-// buffered columns (one per lane; their row indices are read again, from L2
-// shortly after the stream brought them).  Returns the number accepted inline.
+// Store a column that passed the zero count in entry `slot` of its warp's
+// buffer: the index and the packed fingerprints.
+template <int DMAX, bool kWide>
+__device__ __forceinline__ void wbuf_put(int *wb, int slot, int j, const unsigned (&f)[DMAX]) {
+    int *e = wb + slot * kWbufEntry<DMAX>;
+    e[0] = j;
+    constexpr int kPer = kWide ? 2 : 4, kBits = kWide ? 16 : 8;
+#pragma unroll
+    for (int q = 0; q < (DMAX + kPer - 1) / kPer; ++q) {
+        unsigned w = 0u;
+#pragma unroll
+        for (int t = q * kPer; t < DMAX && t < (q + 1) * kPer; ++t) w |= f[t] << (kBits * (t - q * kPer));
+        e[1 + q] = (int)w;
+    }
+}
+
+// The rest of the fingerprint test, then queue (or inline exact score), of
+// up to 32 buffered columns (one per lane), from their packed fingerprints
+// in shared memory; only the columns that pass load their rows (from L2,
+// shortly after the stream brought them).  Returns the number accepted
+// inline.
 template <int DMAX, int THREADS, bool kExactD, bool kWide>
 __device__ __noinline__ int flush_candidates(const EngineArgs &a, const ProblemDev &P,
-                                             const uint8_t *fp, int32_t *queue, int *qn,
-                                             const int *wb, int cnt, bool exact,
-                                             unsigned long long *xmax_s) {
+                                             int32_t *queue, int *qn, const int *wb, int cnt,
+                                             bool exact, unsigned long long *xmax_s) {
     const int lane = threadIdx.x & 31;
     const int d = kExactD ? DMAX : P.d;
     bool acc = false;
     if (lane < cnt) {
-        const int j = wb[lane];
-        int32_t rows[DMAX];
+        const int *e = wb + lane * kWbufEntry<DMAX>;
+        const int j = e[0];
+        constexpr int kPer = kWide ? 2 : 4, kBits = kWide ? 16 : 8;
+        constexpr unsigned kMask = kWide ? 0xffffu : 0xffu;
         unsigned f[DMAX];
         int nz = 0;
 #pragma unroll
         for (int t = 0; t < DMAX; ++t) {
-            rows[t] = (t < d) ? __ldg(P.csc_rows + (size_t)j * d + t) : 0;
-            f[t] = (t < d) ? fp_at<kWide>(fp, rows[t]) : 0u;
+            f[t] = (t < d) ? ((unsigned)e[1 + t / kPer] >> (kBits * (t % kPer))) & kMask : 0u;
             nz += (f[t] != 0u);
         }
         const int need = (a.mode == CCS_SCORE_COUNT) ? a.alpha : a.alpha + (d - nz);
-        if (fp_bound_passes<DMAX, kWide>(f, d, need))
+        if (fp_bound_passes<DMAX, kWide>(f, d, need)) {
+            int32_t rows[DMAX];
+#pragma unroll
+            for (int t = 0; t < DMAX; ++t) rows[t] = (t < d) ? __ldg(P.csc_rows + (size_t)j * d + t) : 0;
             acc = queue_or_score<DMAX, THREADS>(a, P, queue, qn, j, rows, exact, xmax_s, -1);
+        }
     }
     return __popc(__ballot_sync(0xffffffffu, acc));
 }
@@ -573,20 +602,24 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
     const int d = kExactD ? DMAX : P.d;
     const bool use_fp = (P.flags & kPdUseFp) != 0;
     const unsigned lt_mask = (1u << lane) - 1u;
-    int wbn = 0;    // buffered columns of this warp (warp-uniform)
-    int n_acc = 0;  // columns accepted inline by this warp
-    for (int c = 0; c < nchunks; ++c) {
-        const unsigned seq = chunk_seq + c;
-        const int slot = seq % a.stages;
-        ok = ok && mbar_wait(a, &S.full[slot], (seq / a.stages) & 1u);
+    int wbn = 0;     // buffered columns of this warp (warp-uniform)
+    int n_acc = 0;   // columns accepted by the buffer flushes (warp-uniform)
+    int n_mine = 0;  // columns this lane accepted inline
+    // ring slot and phase of chunk c, advanced by one per chunk (no division
+    // in the loop)
+    int slot = (int)(chunk_seq % (unsigned)a.stages);
+    unsigned phase = (chunk_seq / (unsigned)a.stages) & 1u;
+    for (int c = 0; c < nchunks; ++c, slot = (slot + 1 == a.stages) ? (phase ^= 1u, 0) : slot + 1) {
+        ok = ok && mbar_wait(a, &S.full[slot], phase);
         ok = __all_sync(0xffffffffu, ok);  // warp-uniform: the tile loop votes
         const int32_t *stage = reinterpret_cast<const int32_t *>(S.stage + (size_t)slot * a.stage_bytes);
         long long col0, col1;
         chunk_cols(P, sg.lo, sg.hi, c, per, col0, col1);
         // ints of this chunk that came by TMA; only a problem's last chunk
         // can end with up to 3 ints that did not
-        const long long e_tma = (((col1 - col0) * d * 4) & ~15ll) / 4;
-        const bool tail = e_tma != (col1 - col0) * d;
+        const int ncol = (int)(col1 - col0);  // at most (warps - 1) * kTpw * 32
+        const int e_tma = ((ncol * d * 4) & ~15) / 4;
+        const bool tail = e_tma != ncol * d;
 #pragma unroll
         for (int u = 0; u < kTpw; ++u) {
             const int tile = sg.lo + c * per + u * (warps - 1) + (warp - 1);
@@ -594,7 +627,7 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
             const int base = tile * kTile;
             const bool live = lane < P.n - base;
             const int j = base + lane;
-            const long long e0 = (long long)(j - col0) * d;  // first int of column j
+            const int e0 = (j - (int)col0) * d;  // first int of column j in the stage
             int32_t rows[DMAX];
             if (!tail) {
 #pragma unroll
@@ -634,7 +667,7 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
                     if (live && fw != 0u && nz >= need && cf >= need)
                         acc = queue_or_score<DMAX, THREADS>(a, P, S.queue, S.qn, j, rows, exact,
                                                             S.xmax, spos);
-                    n_acc += __popc(__ballot_sync(0xffffffffu, acc));
+                    n_mine += acc;
                     continue;
                 }
                 const bool pass = live && nz >= need;
@@ -649,13 +682,13 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
                         // lanes that did not fit start the next one
                         const int cnt = __popc(bal);
                         const int slot_w = wbn + __popc(bal & lt_mask);
-                        if (pass && slot_w < 32) wb[slot_w] = j;
+                        if (pass && slot_w < 32) wbuf_put<DMAX, kWide>(wb, slot_w, j, f);
                         if (wbn + cnt >= 32) {
                             __syncwarp();
                             n_acc += flush_candidates<DMAX, THREADS, kExactD, kWide>(
-                                a, P, S.fp, S.queue, S.qn, wb, 32, exact, S.xmax);
+                                a, P, S.queue, S.qn, wb, 32, exact, S.xmax);
                             __syncwarp();
-                            if (pass && slot_w >= 32) wb[slot_w - 32] = j;
+                            if (pass && slot_w >= 32) wbuf_put<DMAX, kWide>(wb, slot_w - 32, j, f);
                             wbn += cnt - 32;
                         } else {
                             wbn += cnt;
@@ -663,16 +696,17 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
                     }
                 }
             }
-            n_acc += __popc(__ballot_sync(0xffffffffu, acc));
+            n_mine += acc;
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.empty[slot]);  // this warp is done with the stage
     }
     if (kUseWarpBuffer<THREADS, kWide> && wbn > 0 && ok) {
         __syncwarp();
-        n_acc += flush_candidates<DMAX, THREADS, kExactD, kWide>(a, P, S.fp, S.queue, S.qn, wb,
-                                                                 wbn, exact, S.xmax);
+        n_acc += flush_candidates<DMAX, THREADS, kExactD, kWide>(a, P, S.queue, S.qn, wb, wbn,
+                                                                 exact, S.xmax);
     }
+    n_acc += (int)__reduce_add_sync(0xffffffffu, (unsigned)n_mine);
     if (lane == 0 && n_acc) atomicAdd(S.acc, (unsigned long long)n_acc);
 }
 
@@ -747,10 +781,12 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
                 for (uint32_t off = 0; off < total; off += kFpChunk)
                     bulk_g2s(S.fp + off, P.fp + off, min((uint32_t)kFpChunk, total - off), S.fp_bar);
             }
-            for (int c = pf ? pf->chunks : 0; c < nchunks; ++c) {
-                const unsigned seq = chunk_seq + c;
-                const int slot = seq % a.stages;
-                if (!mbar_wait(a, &S.empty[slot], ((seq / a.stages) & 1u) ^ 1u)) {
+            const int c0 = pf ? pf->chunks : 0;
+            int slot = (int)((chunk_seq + c0) % (unsigned)a.stages);
+            unsigned phase = ((chunk_seq + c0) / (unsigned)a.stages) & 1u;
+            for (int c = c0; c < nchunks;
+                 ++c, slot = (slot + 1 == a.stages) ? (phase ^= 1u, 0) : slot + 1) {
+                if (!mbar_wait(a, &S.empty[slot], phase ^ 1u)) {
                     ok = false;
                     break;
                 }
@@ -761,7 +797,7 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
         if (use_fp) ok = ok && mbar_wait(a, S.fp_bar, fp_seq & 1u);
         if (a.stamps && blockIdx.x == 0 && threadIdx.x == 32 && g < kMaxStampIters)
             a.stamps[kSubBase + 3 * g] = globaltimer();
-        int *wb = S.wbuf + (warp - 1) * kWbufPerWarp;
+        int *wb = S.wbuf + (warp - 1) * kWbufPerWarp * kWbufEntry<DMAX>;
         const bool wide = fp16_for(P.m);
         if (P.d == DMAX) {
             if (wide)
@@ -1312,7 +1348,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
     __shared__ int s_ovf_n;
     __shared__ int s_ovf[kOvfCap];  // rows whose sum needs the whole CSR row
     __shared__ int s_rows_R, s_rows_E, s_rowmode;  // the iteration's row-driven phase
-    __shared__ int s_wbuf[(kWarps - 1) * kWbufPerWarp];
+    __shared__ int s_wbuf[kUseWarpBuffer<THREADS, true>
+                              ? (kWarps - 1) * kWbufPerWarp * kWbufEntry<DMAX> : 1];
     ScoreSmem S;
     S.fp = smem;
     S.stage = reinterpret_cast<char *>(smem + a.fp_cap);

@@ -807,3 +807,24 @@ def test_row_driven_after_dirty_workspace(ccs, orc, m):
         g = ccs.decode_parallel_l0(csc, ptr, cols, y, ws=ws, debug_flags=ROW_ALWAYS)
         assert_same_decode(g, ref)
         assert g.row_driven >= 1
+
+
+@pytest.mark.parametrize("case", ["small", "extreme_2e22", "count", "shifted", "ordered"])
+def test_stream_candidates_scored_inline_match_oracle(ccs, orc, case):
+    """Debug bit 6 scores every candidate of the column stream where it is
+    found instead of queueing it (the path a full queue takes): the decode
+    is the same, bit for bit."""
+    p = {"small": inputs.plain_small(seed=71),
+         "extreme_2e22": inputs.extreme_undersampling(0.08, d=9, seed=72, log2n=22)}.get(
+        case, inputs.make_problem(50000, 5000, 7, 1000, 73))
+    kw = dict(count=dict(score_mode=ccs.SCORE_COUNT, alpha=3), shifted=dict(shifted=True),
+              ordered=dict(debug_flags=2)).get(case, {})
+    okw = {k: v for k, v in kw.items() if k != "debug_flags"}
+    if "score_mode" in okw:
+        okw["score_mode"] = orc.SCORE_COUNT
+    csc, ptr, cols, y = device_problem(ccs, p)
+    A, y_ref = oracle_problem(orc, p)
+    ref = orc.parallel_l0(A, p.m, y_ref, **okw)
+    g = ccs.decode_parallel_l0(csc, ptr, cols, y,
+                               **dict(kw, debug_flags=kw.get("debug_flags", 0) | 64))
+    assert_same_decode(g, ref)
