@@ -153,6 +153,27 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// An L2 policy that marks lines as the first to evict.  The CSC streams
+// through L2 once per score phase (604 MB at n = 2^24, d = 9, several times
+// the L2); with the default policy it evicts r, the fingerprints and the
+// queued candidates' x_hat, whose gathers then wait behind the stream in
+// HBM.  Marked evict-first, the stream replaces its own lines first.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// bulk_g2s with an L2 cache policy for the source lines.
+__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
 // try_wait that may suspend the thread for up to `hint_ns` while the phase
 // is incomplete (it returns as soon as the phase completes), so waiting
 // warps do not spin through issue slots.
@@ -364,7 +385,9 @@ __device__ __forceinline__ void issue_chunk(const EngineArgs &a, const ProblemDe
     const uint32_t tma = (uint32_t)((col1 - col0) * P.d * 4) & ~15u;
     uint64_t *bar = &S.full[slot];
     mbar_expect_tx(bar, tma);
-    if (tma) bulk_g2s(S.stage + (size_t)slot * a.stage_bytes, P.csc_rows + col0 * P.d, tma, bar);
+    if (tma)
+        bulk_g2s_hint(S.stage + (size_t)slot * a.stage_bytes, P.csc_rows + col0 * P.d, tma, bar,
+                      l2_evict_first_policy());
 }
 
 // Copies a one-problem launch issues ahead of its score phase (thread 0's
@@ -482,7 +505,7 @@ __device__ __forceinline__ void score_queue(const EngineArgs &a, const ProblemDe
 #pragma unroll
             for (int t = 0; t < DMAX; ++t) v[t] = (t < d) ? value_bits(__ldcg(P.r + rows[t])) : 0ull;
             const double xj = __ldcg(P.x_hat + j);
-            const uint8_t ins = __ldcg(P.in_slots + j);
+            const uint8_t ins = exact ? (uint8_t)0 : __ldcg(P.in_slots + j);
             unsigned long long omega;
             acc = (spos >= 0) ? exact_score_shifted<DMAX>(v, d, spos, a.alpha, a.mode, &omega)
                               : exact_score_values<DMAX>(v, d, a.alpha, a.mode, &omega);
