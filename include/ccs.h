@@ -428,13 +428,28 @@ typedef struct {
     int32_t n, m, d, reserved;
     uint64_t a_seed;          /* seed of A, as for ccs_make_expander         */
     const double *y;          /* HOST, m measurements                        */
-    double *x_hat;            /* HOST out, n                                 */
+    double *x_hat;            /* HOST out, n; optional when the nonzeros are
+                                 asked for below                             */
     double *r;                /* HOST out, m: y - A x_hat at exit; optional  */
     int64_t *r0_hist;         /* HOST out, max_iter+1 entries; optional      */
+    /* x_hat as its nonzero entries (optional, all three or none): the
+     * server lists them on the device and copies back only those.
+     * *x_nnz = their number nnz; x_idx / x_val receive min(nnz, x_cap) of
+     * them, indices ascending -- all of them when nnz <= x_cap, else an
+     * unspecified subset (ask again with x_cap >= nnz).  A decoded
+     * k-sparse x_hat moves 16 k bytes instead of 8 n. */
+    int64_t *x_idx;           /* HOST out, x_cap entries                     */
+    double *x_val;            /* HOST out, x_cap entries                     */
+    int64_t x_cap;            /* >= 1 when the nonzeros are asked for        */
+    int64_t *x_nnz;           /* HOST out, one entry                         */
 } ccs_seeded_request;
 
-/* Pool bytes one seeded request holds while admitted (0: invalid sizes). */
-CCS_API size_t ccs_seeded_request_bytes(int32_t n, int32_t m, int32_t d, int32_t max_iter);
+/* Pool bytes one seeded request holds while admitted: A, y, x_hat, r, the
+ * history, the decode state, the generation workspace, and 8 + 16 x_cap
+ * for the nonzero list (x_cap = 0 when the request asks for none).  0 for
+ * invalid sizes. */
+CCS_API size_t ccs_seeded_request_bytes(int32_t n, int32_t m, int32_t d, int32_t max_iter,
+                                        int64_t x_cap);
 
 /* Starts the worker on the current device; work goes to `stream`.
  * CCS_EINVAL for a bad configuration, CCS_EBUDGET if the pool cannot even
@@ -446,7 +461,7 @@ CCS_API int ccs_server_create(const ccs_server_config *cfg, ccs_stream_t stream,
 CCS_API int ccs_server_submit(ccs_server *s, const ccs_problem *req, int64_t *ticket);
 /* Queues a seeded request (see ccs_seeded_request).  CCS_EBUDGET if
  * ccs_seeded_request_bytes() can never fit the pool, CCS_EINVAL for bad
- * sizes or null y / x_hat.  A failure while drawing A or copying data ends
+ * sizes, a null y, or neither x_hat nor a complete nonzero-list request.  A failure while drawing A or copying data ends
  * the request with that code in its result's error field. */
 CCS_API int ccs_server_submit_seeded(ccs_server *s, const ccs_seeded_request *req,
                                      int64_t *ticket);

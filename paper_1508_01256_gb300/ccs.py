@@ -63,7 +63,9 @@ class SeededRequest(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32), ("d", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("a_seed", ctypes.c_uint64),
                 ("y", ctypes.c_void_p), ("x_hat", ctypes.c_void_p), ("r", ctypes.c_void_p),
-                ("r0_hist", ctypes.c_void_p)]
+                ("r0_hist", ctypes.c_void_p), ("x_idx", ctypes.c_void_p),
+                ("x_val", ctypes.c_void_p), ("x_cap", ctypes.c_int64),
+                ("x_nnz", ctypes.c_void_p)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -156,7 +158,7 @@ def lib() -> ctypes.CDLL:
         l.ccs_server_submit.argtypes = [P, ctypes.POINTER(Problem), ctypes.POINTER(i64)]
         l.ccs_server_submit_seeded.argtypes = [P, ctypes.POINTER(SeededRequest),
                                                ctypes.POINTER(i64)]
-        l.ccs_seeded_request_bytes.argtypes = [i32, i32, i32, i32]
+        l.ccs_seeded_request_bytes.argtypes = [i32, i32, i32, i32, i64]
         l.ccs_seeded_request_bytes.restype = sz
         l.ccs_server_poll.argtypes = [P, i64, ctypes.POINTER(TicketInfo)]
         l.ccs_server_wait.argtypes = [P, i64, ctypes.POINTER(TicketInfo), i32]
@@ -400,8 +402,8 @@ def ccs_decode_parallel_l0_noalloc(n, m, d, csc_rows, csr_ptr, csr_cols, y, x_ha
     return out
 
 
-def ccs_seeded_request_bytes(n: int, m: int, d: int, max_iter: int = 100) -> int:
-    return int(lib().ccs_seeded_request_bytes(n, m, d, max_iter))
+def ccs_seeded_request_bytes(n: int, m: int, d: int, max_iter: int = 100, x_cap: int = 0) -> int:
+    return int(lib().ccs_seeded_request_bytes(n, m, d, max_iter, x_cap))
 
 
 def ccs_noalloc_scratch_bytes() -> int:
@@ -646,12 +648,14 @@ class Server:
         self._keep[t.value] = (csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist)
         return t.value
 
-    def submit_seeded(self, n: int, m: int, d: int, a_seed: int, y, x_hat, r=None,
-                      r0_hist=None) -> int:
+    def submit_seeded(self, n: int, m: int, d: int, a_seed: int, y, x_hat=None, r=None,
+                      r0_hist=None, nonzeros=None) -> int:
         """A request whose A the server draws from `a_seed` into its pool
         (ccs_server_submit_seeded).  y, x_hat, r, r0_hist are HOST numpy
         arrays (float64 m, float64 n, float64 m, int64 >= max_iter + 1),
-        kept alive here until the result is collected."""
+        kept alive here until the result is collected.  nonzeros = (idx
+        int64[cap], val float64[cap], nnz int64[1]) asks for x_hat as its
+        nonzero entries instead of (or besides) the dense x_hat."""
         import numpy as np
 
         def need(a, dtype, size, name, at_least=False):
@@ -660,18 +664,32 @@ class Server:
                 raise ValueError(f"{name}: need a contiguous {np.dtype(dtype)} numpy array "
                                  f"of {'at least ' if at_least else ''}{size} elements")
         need(y, np.float64, m, "y")
-        need(x_hat, np.float64, n, "x_hat")
+        if x_hat is None and nonzeros is None:
+            raise ValueError("need x_hat or nonzeros")
+        if x_hat is not None:
+            need(x_hat, np.float64, n, "x_hat")
         if r is not None:
             need(r, np.float64, m, "r")
         if r0_hist is not None:
             need(r0_hist, np.int64, self.max_iter + 1, "r0_hist", at_least=True)
-        req = SeededRequest(n, m, d, 0, a_seed & (2 ** 64 - 1), y.ctypes.data, x_hat.ctypes.data,
+        cap, nz_args = 0, (None, None, 0, None)
+        if nonzeros is not None:
+            idx, val, nnz = nonzeros
+            cap = idx.size if isinstance(idx, np.ndarray) else 0
+            if cap < 1:
+                raise ValueError("nonzeros: idx needs at least one entry")
+            need(idx, np.int64, cap, "nonzeros idx")
+            need(val, np.float64, cap, "nonzeros val")
+            need(nnz, np.int64, 1, "nonzeros nnz")
+            nz_args = (idx.ctypes.data, val.ctypes.data, cap, nnz.ctypes.data)
+        req = SeededRequest(n, m, d, 0, a_seed & (2 ** 64 - 1), y.ctypes.data,
+                            x_hat.ctypes.data if x_hat is not None else None,
                             r.ctypes.data if r is not None else None,
-                            r0_hist.ctypes.data if r0_hist is not None else None)
+                            r0_hist.ctypes.data if r0_hist is not None else None, *nz_args)
         t = ctypes.c_int64()
         _check(lib().ccs_server_submit_seeded(self._h, ctypes.byref(req), ctypes.byref(t)),
                "ccs_server_submit_seeded")
-        self._keep[t.value] = (y, x_hat, r, r0_hist)
+        self._keep[t.value] = (y, x_hat, r, r0_hist, nonzeros)
         return t.value
 
     def poll(self, ticket: int):
@@ -795,11 +813,13 @@ def serve_stream(server: Server, request_of, count: int, arrivals_s, ring: int,
 
 
 def serve_seeded(server: Server, requests, arrivals_s, on_done, timeout_ms: int = 120000,
-                 sampler=None, sample_every_s: float = 0.002):
+                 sampler=None, sample_every_s: float = 0.002, nonzeros_cap=None):
     """Open-loop serving of seeded requests: requests[q] = (n, m, d, a_seed,
     y host array) is submitted at arrivals_s[q] (seconds from now) with a
-    fresh host x_hat buffer; when its result arrives (collected in
-    submission order) on_done(q, info, x_hat) is called and the buffer is
+    fresh host x_hat buffer -- or, with nonzeros_cap(q) given, fresh
+    (idx, val, nnz) buffers for x_hat's nonzeros; when its result arrives
+    (collected in submission order) on_done(q, info, out) is called (out:
+    the x_hat array, or the (idx, val, nnz) tuple) and the buffers are
     released.  With `sampler` (a list), (t, inflight, pending, bytes_in_use)
     from ccs_server_stats is appended every `sample_every_s` while requests
     are outstanding.  Returns the TicketInfo list in submission order."""
@@ -847,9 +867,16 @@ def serve_seeded(server: Server, requests, arrivals_s, on_done, timeout_ms: int 
             time.sleep(delay)
         if state["error"] is not None:
             break
-        x = np.empty(n, dtype=np.float64)
-        bufs[q] = x
-        tickets.append(server.submit_seeded(n, m, d, a_seed, y, x))
+        if nonzeros_cap is None:
+            x = np.empty(n, dtype=np.float64)
+            bufs[q] = x
+            tickets.append(server.submit_seeded(n, m, d, a_seed, y, x))
+        else:
+            cap = max(1, int(nonzeros_cap(q)))
+            nz = (np.empty(cap, dtype=np.int64), np.empty(cap, dtype=np.float64),
+                  np.zeros(1, dtype=np.int64))
+            bufs[q] = nz
+            tickets.append(server.submit_seeded(n, m, d, a_seed, y, None, nonzeros=nz))
     th.join()
     if ts is not None:
         ts.join()

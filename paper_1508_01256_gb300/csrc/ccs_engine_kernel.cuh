@@ -400,13 +400,17 @@ struct Prefetch {
     bool fp;     // the next fingerprint copy is in flight
 };
 
-// Issue the first chunks of a segment (up to the ring depth) ahead of its
-// score phase.  Thread 0 only; the ring's previous chunks are all consumed.
+// Issue the first chunk of a segment ahead of its score phase (the producer
+// issues the rest when the phase begins).  Only one: the fingerprint copy
+// issued just before must land before any column can be tested, and a whole
+// ring of chunks from HBM would share the SM's bandwidth with it (measured:
+// the fingerprint wait drops from ~8 us to ~5 us at n = 2^24).  Thread 0
+// only; the ring's previous chunks are all consumed.
 __device__ __forceinline__ void prefetch_chunks(const EngineArgs &a, const ProblemDev &P, int lo,
                                                 int hi, int per, ScoreSmem &S, unsigned chunk_seq,
                                                 Prefetch &pf, bool &ok) {
     const int nchunks = (hi - lo + per - 1) / per;
-    const int c1 = min(nchunks, a.stages);
+    const int c1 = min(nchunks, 1);
     for (int c = pf.chunks; c < c1; ++c) {
         const unsigned seq = chunk_seq + c;
         const int slot = seq % a.stages;
@@ -1415,7 +1419,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
 
     // a lone problem: this CTA's column tiles are the same in every
     // iteration, so once the stop rule has let the problem run another
-    // iteration, the fingerprint copy and the first CSC chunks of that score
+    // iteration, the fingerprint copy and the first CSC chunk of that score
     // phase are issued at once, ahead of the iteration's set-up (thread 0
     // keeps the record in shared memory)
     __shared__ Prefetch pf;

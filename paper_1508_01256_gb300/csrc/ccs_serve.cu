@@ -26,6 +26,7 @@
 //    the server uses.  When the request finishes, x_hat (and r, the ||r||_0
 //    history if asked for) are copied to the caller's host buffers, and
 //    only then is its memory returned to the pool and its result published.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -91,6 +92,10 @@ class PoolAllocator {
     std::map<size_t, size_t> free_;
 };
 
+// Pinned host staging for the nonzero lists that leave the server in one
+// round (a list that does not fit is copied on its own).
+constexpr size_t kStagingBytes = 32u << 20;
+
 struct Request {
     int64_t ticket;
     ccs_problem prob;     // device arrays (for a seeded request: pool memory,
@@ -123,6 +128,8 @@ struct ccs_server {
     std::unordered_map<int64_t, ccs::Request> finished;
     int64_t next_ticket = 1;
     int *host_max = nullptr;  // pinned: largest row degree per seeded request being prepared
+    unsigned long long *host_cnt = nullptr;  // pinned: nonzeros of each finished seeded request
+    char *staging = nullptr;  // pinned: the finished requests' nonzero lists, on their way out
     bool stop = false;
     int error = CCS_OK;
     ccs_server_stats stats{};
@@ -139,8 +146,9 @@ static size_t request_state_bytes(int32_t n, int32_t m) {
 // CSR columns, y, x_hat, r, the ||r||_0 history and the expander's
 // generation workspace.  Returns the total bytes; with base != null fills
 // the request's device pointers (and *gen_ws).
-static size_t seeded_layout(int32_t n, int32_t m, int32_t d, int32_t max_iter, char *base,
-                            ccs_problem *prob, char **gen_ws, size_t *gen_bytes) {
+static size_t seeded_layout(int32_t n, int32_t m, int32_t d, int32_t max_iter, int64_t x_cap,
+                            char *base, ccs_problem *prob, char **gen_ws, size_t *gen_bytes,
+                            char **sparse = nullptr) {
     size_t off = align_up(request_state_bytes(n, m), 256);
     auto take = [&](size_t bytes) {
         char *p = base ? base + off : nullptr;
@@ -156,6 +164,10 @@ static size_t seeded_layout(int32_t n, int32_t m, int32_t d, int32_t max_iter, c
     char *hist = take(((size_t)max_iter + 1) * 8);
     const size_t gb = ccs_workspace_size(CCS_OP_MAKE_EXPANDER, n, m, d);
     char *gw = take(gb);
+    // the nonzeros of x_hat when the request asks for them: a count, then
+    // x_cap indices and x_cap values
+    char *sp = x_cap > 0 ? take(8 + 16 * (size_t)x_cap) : nullptr;
+    if (sparse) *sparse = sp;
     if (base) {
         prob->csc_rows = reinterpret_cast<const int32_t *>(csc);
         prob->csr_ptr = reinterpret_cast<const int64_t *>(ptr);
@@ -186,8 +198,8 @@ static void prepare_seeded(ccs_server *S, const std::vector<int> &todo, std::vec
         Request &R = S->inflight[todo[q]];
         const ccs_seeded_request &h = R.host;
         size_t gen_bytes = 0;
-        seeded_layout(h.n, h.m, h.d, S->cfg.params.max_iter, S->pool + R.off, &R.prob, &gen[q],
-                      &gen_bytes);
+        seeded_layout(h.n, h.m, h.d, S->cfg.params.max_iter, h.x_idx ? h.x_cap : 0,
+                      S->pool + R.off, &R.prob, &gen[q], &gen_bytes);
         if (cudaMemcpyAsync(const_cast<double *>(R.prob.y), h.y, (size_t)h.m * 8,
                             cudaMemcpyHostToDevice, S->stream) != cudaSuccess)
             rcs[q] = cuda_fail(cudaGetLastError(), "server: upload of y");
@@ -220,19 +232,152 @@ static void prepare_seeded(ccs_server *S, const std::vector<int> &todo, std::vec
     }
 }
 
-// Seeded request finished: its outputs to the caller's host buffers.
-static int deliver_seeded(ccs_server *S, const Request &R) {
-    const ccs_seeded_request &h = R.host;
-    cudaError_t e = cudaMemcpyAsync(h.x_hat, R.prob.x_hat, (size_t)h.n * 8,
-                                    cudaMemcpyDeviceToHost, S->stream);
-    if (e == cudaSuccess && h.r)
-        e = cudaMemcpyAsync(h.r, R.prob.r, (size_t)h.m * 8, cudaMemcpyDeviceToHost, S->stream);
-    if (e == cudaSuccess && h.r0_hist)
-        e = cudaMemcpyAsync(h.r0_hist, R.prob.r0_hist,
-                            ((size_t)R.result.iterations + 1) * 8, cudaMemcpyDeviceToHost,
-                            S->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
-    return e == cudaSuccess ? CCS_OK : cuda_fail(e, "server: copy of the results to the host");
+// Nonzero entries of x[0, n) as (index, value) pairs, at most cap of them, in
+// no particular order; *count receives how many there are.  One warp
+// reservation per 32 entries.
+__global__ void k_nonzeros(int32_t n, const double *__restrict__ x, int64_t *idx, double *val,
+                           int64_t cap, unsigned long long *count) {
+    const int lane = threadIdx.x & 31;
+    for (long long j0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); j0 < n;
+         j0 += (long long)gridDim.x * blockDim.x) {
+        const long long j = j0 + lane;
+        const double v = j < n ? x[j] : 0.0;
+        const unsigned bal = __ballot_sync(0xffffffffu, v != 0.0);
+        if (!bal) continue;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(count, (unsigned long long)__popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (v != 0.0) {
+            const unsigned long long k = base + __popc(bal & ((1u << lane) - 1u));
+            if ((long long)k < cap) {
+                idx[k] = j;
+                val[k] = v;
+            }
+        }
+    }
+}
+
+// Seeded requests finished in this round: their outputs to the callers' host
+// buffers.  Every request's device work (the nonzero lists) is enqueued
+// first, with one wait for all counts; then the host copies.  rcs[q]
+// receives each request's status.
+static void deliver_seeded(ccs_server *S, std::vector<Request *> &done, std::vector<int> &rcs) {
+    const int Q = (int)done.size();
+    rcs.assign(Q, CCS_OK);
+    std::vector<char *> sp(Q, nullptr);
+    for (int q = 0; q < Q; ++q) {
+        Request &R = *done[q];
+        const ccs_seeded_request &h = R.host;
+        if (!h.x_idx) continue;
+        char *gen = nullptr;
+        size_t gen_bytes = 0;
+        ccs_problem unused;
+        seeded_layout(h.n, h.m, h.d, S->cfg.params.max_iter, h.x_cap, S->pool + R.off, &unused,
+                      &gen, &gen_bytes, &sp[q]);
+        unsigned long long *cnt = reinterpret_cast<unsigned long long *>(sp[q]);
+        if (cudaMemsetAsync(cnt, 0, 8, S->stream) != cudaSuccess) {
+            rcs[q] = cuda_fail(cudaGetLastError(), "server: nonzero count");
+            continue;
+        }
+        const int blocks = std::max(1, std::min(1024, (h.n + 255) / 256));
+        k_nonzeros<<<blocks, 256, 0, S->stream>>>(h.n, R.prob.x_hat,
+                                                  reinterpret_cast<int64_t *>(sp[q] + 8),
+                                                  reinterpret_cast<double *>(sp[q] + 8 + 8 * h.x_cap),
+                                                  h.x_cap, cnt);
+        count_launches(1);
+        if (cudaMemcpyAsync(S->host_cnt + q, cnt, 8, cudaMemcpyDeviceToHost, S->stream) !=
+            cudaSuccess)
+            rcs[q] = cuda_fail(cudaGetLastError(), "server: read-back of the nonzero count");
+    }
+    if (cudaStreamSynchronize(S->stream) != cudaSuccess) {
+        const int rc = cuda_fail(cudaGetLastError(), "server: nonzero lists");
+        for (int q = 0; q < Q; ++q) rcs[q] = rcs[q] ? rcs[q] : rc;
+        return;
+    }
+    // the dense copies go straight to the callers' buffers; the nonzero
+    // lists go to the server's pinned staging area first (one wait for all
+    // of them), then are ordered into the callers' buffers
+    std::vector<long long> stage_off(Q, -1), nnz(Q, 0), take(Q, 0);
+    size_t used = 0;
+    for (int q = 0; q < Q; ++q) {
+        if (rcs[q]) continue;
+        const Request &R = *done[q];
+        const ccs_seeded_request &h = R.host;
+        cudaError_t e = cudaSuccess;
+        if (h.x_hat)
+            e = cudaMemcpyAsync(h.x_hat, R.prob.x_hat, (size_t)h.n * 8, cudaMemcpyDeviceToHost,
+                                S->stream);
+        if (e == cudaSuccess && h.r)
+            e = cudaMemcpyAsync(h.r, R.prob.r, (size_t)h.m * 8, cudaMemcpyDeviceToHost, S->stream);
+        if (e == cudaSuccess && h.r0_hist)
+            e = cudaMemcpyAsync(h.r0_hist, R.prob.r0_hist,
+                                ((size_t)R.result.iterations + 1) * 8, cudaMemcpyDeviceToHost,
+                                S->stream);
+        if (e == cudaSuccess && h.x_idx) {
+            nnz[q] = (long long)S->host_cnt[q];
+            take[q] = std::min<long long>(nnz[q], h.x_cap);
+            const size_t bytes = (size_t)take[q] * 16;
+            if (bytes <= kStagingBytes - used) {
+                stage_off[q] = (long long)used;
+                if (take[q])
+                    e = cudaMemcpyAsync(S->staging + used, sp[q] + 8, (size_t)take[q] * 8,
+                                        cudaMemcpyDeviceToHost, S->stream);
+                if (e == cudaSuccess && take[q])
+                    e = cudaMemcpyAsync(S->staging + used + (size_t)take[q] * 8,
+                                        sp[q] + 8 + 8 * h.x_cap, (size_t)take[q] * 8,
+                                        cudaMemcpyDeviceToHost, S->stream);
+                used += bytes;
+            }
+        }
+        if (e != cudaSuccess) rcs[q] = cuda_fail(e, "server: copy of the results to the host");
+    }
+    if (cudaStreamSynchronize(S->stream) != cudaSuccess) {
+        const int rc = cuda_fail(cudaGetLastError(), "server: copy of the results to the host");
+        for (int q = 0; q < Q; ++q) rcs[q] = rcs[q] ? rcs[q] : rc;
+        return;
+    }
+    std::vector<std::pair<int64_t, double>> pairs;
+    std::vector<int64_t> ix;
+    std::vector<double> vx;
+    for (int q = 0; q < Q; ++q) {
+        if (rcs[q] || !done[q]->host.x_idx) continue;
+        const ccs_seeded_request &h = done[q]->host;
+        const long long k = take[q];
+        const int64_t *pi;
+        const double *pv;
+        if (stage_off[q] >= 0) {  // staged
+            pi = reinterpret_cast<const int64_t *>(S->staging + stage_off[q]);
+            pv = reinterpret_cast<const double *>(S->staging + stage_off[q] + (size_t)k * 8);
+        } else {  // larger than the staging area: straight copies
+            ix.resize((size_t)k);
+            vx.resize((size_t)k);
+            char *gen = nullptr;
+            size_t gen_bytes = 0;
+            ccs_problem unused;
+            char *spq = nullptr;
+            seeded_layout(h.n, h.m, h.d, S->cfg.params.max_iter, h.x_cap, S->pool + done[q]->off,
+                          &unused, &gen, &gen_bytes, &spq);
+            cudaError_t e = cudaMemcpy(ix.data(), spq + 8, (size_t)k * 8, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(vx.data(), spq + 8 + 8 * h.x_cap, (size_t)k * 8,
+                               cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                rcs[q] = cuda_fail(e, "server: copy of the nonzeros to the host");
+                continue;
+            }
+            pi = ix.data();
+            pv = vx.data();
+        }
+        // ascending indices (the device list has no order)
+        pairs.resize((size_t)k);
+        for (long long t = 0; t < k; ++t) pairs[(size_t)t] = {pi[t], pv[t]};
+        std::sort(pairs.begin(), pairs.end());
+        for (long long t = 0; t < k; ++t) {
+            h.x_idx[t] = pairs[(size_t)t].first;
+            h.x_val[t] = pairs[(size_t)t].second;
+        }
+        *h.x_nnz = nnz[q];
+    }
 }
 
 static void worker_loop(ccs_server *S) {
@@ -328,13 +473,20 @@ static void worker_loop(ccs_server *S) {
         // finished seeded requests hand their outputs to the host before their
         // memory returns to the pool (outside the lock: it waits on the stream)
         std::vector<int> deliver_rc(P, CCS_OK);
-        for (int p = 0; p < P; ++p) {
-            Request &R = S->inflight[p];
-            const bool done = rc != CCS_OK || res[p].status != kRunning || res[p].error;
-            if (done && R.seeded && rc == CCS_OK) {
-                R.result = res[p];
-                deliver_rc[p] = deliver_seeded(S, R);
+        {
+            std::vector<Request *> fin;
+            std::vector<int> at, rcs;
+            for (int p = 0; p < P; ++p) {
+                Request &R = S->inflight[p];
+                const bool done = rc != CCS_OK || res[p].status != kRunning || res[p].error;
+                if (done && R.seeded && rc == CCS_OK) {
+                    R.result = res[p];
+                    fin.push_back(&R);
+                    at.push_back(p);
+                }
             }
+            if (!fin.empty()) deliver_seeded(S, fin, rcs);
+            for (size_t q = 0; q < at.size(); ++q) deliver_rc[at[q]] = rcs[q];
         }
         {
             std::lock_guard<std::mutex> lk(S->mu);
@@ -400,7 +552,14 @@ extern "C" int ccs_server_create(const ccs_server_config *cfg, ccs_stream_t stre
     S->header_off = (cfg->pool_bytes - hdr) & ~(size_t)255;
     S->alloc = new PoolAllocator(S->header_off);
     if (cudaHostAlloc(reinterpret_cast<void **>(&S->host_max), sizeof(int) * cfg->max_batch,
+                      cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void **>(&S->host_cnt),
+                      sizeof(unsigned long long) * cfg->max_batch,
+                      cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void **>(&S->staging), kStagingBytes,
                       cudaHostAllocDefault) != cudaSuccess) {
+        if (S->host_max) cudaFreeHost(S->host_max);
+        if (S->host_cnt) cudaFreeHost(S->host_cnt);
         delete S->alloc;
         delete S;
         return cuda_fail(cudaGetLastError(), "ccs_server_create: pinned host buffer");
@@ -449,9 +608,10 @@ extern "C" int ccs_server_submit(ccs_server *S, const ccs_problem *req, int64_t 
     return CCS_OK;
 }
 
-extern "C" size_t ccs_seeded_request_bytes(int32_t n, int32_t m, int32_t d, int32_t max_iter) {
-    if (check_sizes(n, m, d) != CCS_OK || max_iter < 0) return 0;
-    return seeded_layout(n, m, d, max_iter, nullptr, nullptr, nullptr, nullptr);
+extern "C" size_t ccs_seeded_request_bytes(int32_t n, int32_t m, int32_t d, int32_t max_iter,
+                                           int64_t x_cap) {
+    if (check_sizes(n, m, d) != CCS_OK || max_iter < 0 || x_cap < 0) return 0;
+    return seeded_layout(n, m, d, max_iter, x_cap, nullptr, nullptr, nullptr, nullptr);
 }
 
 extern "C" int ccs_server_submit_seeded(ccs_server *S, const ccs_seeded_request *req,
@@ -463,8 +623,11 @@ extern "C" int ccs_server_submit_seeded(ccs_server *S, const ccs_seeded_request 
     int rc = check_sizes(req->n, req->m, req->d);
     if (rc) return rc;
     if ((rc = check_params(&S->cfg.params, req->d))) return rc;
-    if (!req->y || !req->x_hat) {
-        set_last_error("ccs_server_submit_seeded: null y or x_hat");
+    const bool sparse = req->x_idx || req->x_val || req->x_nnz;
+    if (!req->y || (!req->x_hat && !sparse) ||
+        (sparse && (!req->x_idx || !req->x_val || !req->x_nnz || req->x_cap < 1))) {
+        set_last_error("ccs_server_submit_seeded: need y and x_hat, or x_idx, x_val, x_nnz and "
+                       "x_cap >= 1");
         return CCS_EINVAL;
     }
     Request R;
@@ -473,8 +636,8 @@ extern "C" int ccs_server_submit_seeded(ccs_server *S, const ccs_seeded_request 
     R.prob.n = req->n;
     R.prob.m = req->m;
     R.prob.d = req->d;
-    R.state_bytes = seeded_layout(req->n, req->m, req->d, S->cfg.params.max_iter, nullptr,
-                                  nullptr, nullptr, nullptr);
+    R.state_bytes = seeded_layout(req->n, req->m, req->d, S->cfg.params.max_iter,
+                                  sparse ? req->x_cap : 0, nullptr, nullptr, nullptr, nullptr);
     if (R.state_bytes > S->alloc->size()) {
         set_last_error("ccs_server_submit_seeded: request needs %zu bytes, pool holds %zu",
                        R.state_bytes, S->alloc->size());
@@ -559,6 +722,8 @@ extern "C" int ccs_server_destroy(ccs_server *S) {
     if (S->worker.joinable()) S->worker.join();
     const int err = S->error;
     cudaFreeHost(S->host_max);
+    cudaFreeHost(S->host_cnt);
+    cudaFreeHost(S->staging);
     delete S->alloc;
     delete S;
     return err;

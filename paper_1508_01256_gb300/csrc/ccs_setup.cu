@@ -206,6 +206,62 @@ __global__ void k_sort_rows(int m, int cap, const int64_t *ptr, int32_t *csr_col
     (void)cap;
 }
 
+// Rows of at most 32 E columns: one warp a row, the row in registers (E per
+// lane, element lane * E + e), bitonic sort by register exchanges and warp
+// shuffles: no shared memory and no block barriers.
+template <int E>
+__global__ void k_sort_rows_warp(int m, const int64_t *ptr, int32_t *csr_cols) {
+    constexpr int kCap = 32 * E;
+    const int lane = threadIdx.x & 31;
+    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = w0; i < m; i += nw) {
+        const int64_t b = ptr[i];
+        const int len = (int)(ptr[i + 1] - b);
+        if (len <= 1) continue;
+        int32_t v[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int idx = lane * E + e;
+            v[e] = idx < len ? csr_cols[b + idx] : 0x7fffffff;
+        }
+#pragma unroll
+        for (int k = 2; k <= kCap; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                if (j < E) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int p = e ^ j;
+                        if (p > e) {
+                            const bool up = ((lane * E + e) & k) == 0;
+                            const int32_t a = v[e], c = v[p];
+                            if ((a > c) == up) {
+                                v[e] = c;
+                                v[p] = a;
+                            }
+                        }
+                    }
+                } else {
+                    const int lj = j / E;
+                    const bool lower = (lane & lj) == 0;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int32_t o = __shfl_xor_sync(0xffffffffu, v[e], lj);
+                        const bool up = ((lane * E + e) & k) == 0;
+                        v[e] = (lower == up) ? min(v[e], o) : max(v[e], o);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int idx = lane * E + e;
+            if (idx < len) csr_cols[b + idx] = v[e];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // y = A x: one warp per row, ascending column order
 // ---------------------------------------------------------------------------
@@ -436,7 +492,21 @@ int expander_sort_rows(int32_t m, int64_t *csr_ptr, int32_t *csr_cols, int host_
                        kMaxSortRow);
         return CCS_EINVAL;
     }
-    if (host_max > 1) {
+    if (host_max > 1 && host_max <= 1024) {
+        // rows of at most 1024 columns: a warp a row, in registers
+        int cap = 32;
+        while (cap < host_max) cap <<= 1;
+        const int grid = 152 * 16, threads = 256;
+        switch (cap) {
+            case 32: k_sort_rows_warp<1><<<grid, threads, 0, s>>>(m, csr_ptr, csr_cols); break;
+            case 64: k_sort_rows_warp<2><<<grid, threads, 0, s>>>(m, csr_ptr, csr_cols); break;
+            case 128: k_sort_rows_warp<4><<<grid, threads, 0, s>>>(m, csr_ptr, csr_cols); break;
+            case 256: k_sort_rows_warp<8><<<grid, threads, 0, s>>>(m, csr_ptr, csr_cols); break;
+            case 512: k_sort_rows_warp<16><<<grid, threads, 0, s>>>(m, csr_ptr, csr_cols); break;
+            default: k_sort_rows_warp<32><<<grid, threads, 0, s>>>(m, csr_ptr, csr_cols); break;
+        }
+        CCS_CUDA_TRY(cudaGetLastError());
+    } else if (host_max > 1) {
         int cap = 2;
         while (cap < host_max) cap <<= 1;
         const size_t smem = (size_t)cap * 4;

@@ -27,7 +27,7 @@ def ccs():
 
 EXPANDER_SIZES = [(1, 1, 1), (5, 5, 5), (1000, 97, 1), (1000, 97, 2), (3001, 211, 3),
                   (4096, 410, 7), (777, 16, 16), (20000, 1000, 11), (2 ** 20, 2 ** 17, 7),
-                  (2 ** 20, 1049, 9)]
+                  (2 ** 20, 1049, 9), (65536, 16384, 5), (300000, 2500, 7)]
 
 
 @pytest.mark.parametrize("n,m,d", EXPANDER_SIZES)

@@ -234,3 +234,34 @@ def test_seeded_admission_bounds_the_pool(ccs, orc):
         ref = orc.parallel_l0(A, p.m, y)
         assert info.result.status == ref["status"]
         assert np.array_equal(xo, ref["x_hat"])
+
+
+def test_seeded_nonzero_outputs_equal_the_oracle(ccs, orc):
+    """Seeded requests that ask for x_hat as its nonzeros: the count equals
+    the oracle's, the indices come back ascending with their values bit for
+    bit; with a list too short for every nonzero the count is still exact
+    and the entries returned are nonzeros of the oracle's x_hat."""
+    shapes = [(4096, 410, 7, 41), (20000, 2000, 9, 400), (30000, 300, 7, 90),
+              (12000, 1200, 7, 360)]
+    seeded = _seeded_inputs(orc, shapes, 6100)
+    caps = [1000, 1000, 1000, 7]
+    outs = [(np.zeros(c, dtype=np.int64), np.zeros(c), np.full(1, -1, dtype=np.int64))
+            for c in caps]
+    with ccs.Server(512 << 20, max_batch=8, iters_per_round=2) as srv:
+        tickets = [srv.submit_seeded(p.n, p.m, p.d, p.a_seed, y, None, nonzeros=nz)
+                   for (p, _, y), nz in zip(seeded, outs)]
+        infos = [srv.wait(t) for t in tickets]
+        with pytest.raises(ValueError):
+            srv.submit_seeded(4096, 410, 7, 1, np.zeros(410))  # neither output form
+    for (p, A, y), (idx, val, nnz), cap, info in zip(seeded, outs, caps, infos):
+        ref = orc.parallel_l0(A, p.m, y)
+        assert info.result.error == 0 and info.result.status == ref["status"]
+        want = np.nonzero(ref["x_hat"])[0]
+        assert nnz[0] == want.size
+        got = idx[:min(cap, want.size)]
+        assert np.all(np.diff(got) > 0)
+        assert np.array_equal(val[:got.size].view(np.int64), ref["x_hat"][got].view(np.int64))
+        if want.size <= cap:
+            assert np.array_equal(got, want)
+        else:
+            assert np.isin(got, want).all()
