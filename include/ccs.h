@@ -159,7 +159,20 @@ typedef struct {
                              nonzero r_i instead of streaming every column
                              (same results)                                  */
     int64_t row_entries;  /* CSR entries those score phases read            */
+    int32_t residual_form;/* how r = y - A x_hat was kept when the decode
+                             ended (same results either way):
+                             CCS_RESIDUAL_EXACT or CCS_RESIDUAL_ORDERED      */
+    int32_t reserved;
 } ccs_result;
+
+/* ccs_result.residual_form.  Alg. 2 recomputes r_i = y_i minus the ordered
+ * sum of the row's nonzero x_hat_j.  While every value of the decode lies on
+ * the grid of y and far enough below 2^53 grid steps, binary64 additions are
+ * exact and the persistent engine keeps r by subtracting each accepted omega
+ * instead (EXACT; the bound is checked before every iteration).  Once it
+ * fails, the decode recomputes every touched row by its ordered sum for the
+ * rest of the decode (ORDERED; the host-driven engine always does). */
+enum { CCS_RESIDUAL_EXACT = 0, CCS_RESIDUAL_ORDERED = 1 };
 
 /* One problem of a batch: sizes and caller-owned device arrays. */
 typedef struct {

@@ -24,6 +24,7 @@ CONVERGED, STALLED, MAX_ITER = 0, 1, 2
 STATUS_NAMES = {CONVERGED: "converged", STALLED: "stalled", MAX_ITER: "max_iter"}
 SCORE_L0_DECREASE, SCORE_COUNT = 0, 1
 ENGINE_AUTO, ENGINE_HOST_LOOP, ENGINE_PERSISTENT = 0, 1, 3
+RESIDUAL_EXACT, RESIDUAL_ORDERED = 0, 1
 OP_MAKE_EXPANDER, OP_DECODE = 0, 1
 
 
@@ -47,7 +48,8 @@ class Params(ctypes.Structure):
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
                 ("r0_final", ctypes.c_int64), ("error", ctypes.c_int32),
-                ("row_driven", ctypes.c_int32), ("row_entries", ctypes.c_int64)]
+                ("row_driven", ctypes.c_int32), ("row_entries", ctypes.c_int64),
+                ("residual_form", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Problem(ctypes.Structure):
@@ -539,7 +541,8 @@ def decode_parallel_l0(csc_rows, csr_ptr, csr_cols, y, alpha=2, max_iter=100,
     h = hist[:res.iterations + 1].cpu().tolist() if hist is not None else None
     return DecodeOutput(x_hat=x_hat, r=r, r0_hist=h, status=res.status,
                         iterations=res.iterations, r0_final=res.r0_final, error=res.error,
-                        row_driven=res.row_driven, row_entries=res.row_entries)
+                        row_driven=res.row_driven, row_entries=res.row_entries,
+                        residual_form=res.residual_form)
 
 
 def problem(csc_rows, csr_ptr, csr_cols, y, x_hat, r, r0_hist=None,
@@ -577,7 +580,7 @@ def decode_batch(items, alpha=2, max_iter=100, score_mode=SCORE_L0_DECREASE,
         h = hist[:rr.iterations + 1].cpu().tolist() if hist is not None else None
         result.append(DecodeOutput(x_hat=x_hat, r=r, r0_hist=h, status=rr.status,
                                    iterations=rr.iterations, r0_final=rr.r0_final,
-                                   error=rr.error))
+                                   error=rr.error, residual_form=rr.residual_form))
     return result
 
 

@@ -233,6 +233,8 @@ int decode_host_loop(const ProblemDev &P, const ccs_params &p, ccs_result *out,
     out->error = (h.error & kErrWatchdog) ? CCS_ETIMEOUT : CCS_OK;
     out->row_driven = 0;
     out->row_entries = 0;
+    out->residual_form = CCS_RESIDUAL_ORDERED;
+    out->reserved = 0;
     return out->error;
 }
 

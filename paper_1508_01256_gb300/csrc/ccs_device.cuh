@@ -373,26 +373,40 @@ __device__ __forceinline__ void load_record(const ProblemDev &P, int i, int (&js
     }
 }
 
-// Sum of v[j] over row i's CSR columns in ascending j, from +0.0, skipping
-// zero entries, by the whole warp.  The lanes fetch 8 x 32 consecutive
-// entries at a time (eight independent loads each, then eight gathers), and
-// the nonzero ones are added chunk by chunk in lane order, so the order of
-// the additions is exactly the sequential one.  Result valid in every lane.
-__device__ __forceinline__ double warp_ordered_row_sum(const int64_t *ptr, const int32_t *cols,
-                                                       const double *v, int i, int lane) {
-    constexpr int kU = 8;
+// Sum of the nonzero x_hat_j over row i's CSR columns in ascending j, from
+// +0.0, by the whole warp: the lanes take 32 kU consecutive entries at a
+// time and the nonzero values are added chunk by chunk in lane order, so the
+// order of the additions is exactly the sequential one.  Only columns whose
+// in-slots flag is set are gathered: the flag is a superset of x_hat_j != 0
+// (a column sets it the first time it turns nonzero), so a long row with
+// few nonzero contributors reads its column indices and flag bytes (which
+// stay in L2: the indices stream past with an evict-first load) instead of
+// gathering x_hat_j for every entry.  The next 32 kU indices are loaded
+// while the current ones are looked up.  Result valid in every lane.
+__device__ __forceinline__ double warp_ordered_row_sum_flagged(const ProblemDev &P, int i,
+                                                               int lane) {
+    constexpr int kU = 16;
     double s = 0.0;
-    const int64_t b = __ldg(ptr + i), e = __ldg(ptr + i + 1);
+    const int64_t b = __ldg(P.csr_ptr + i), e = __ldg(P.csr_ptr + i + 1);
+    int c[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+        const int64_t p = b + 32 * u + lane;
+        c[u] = (p < e) ? __ldcs(P.csr_cols + p) : -1;
+    }
     for (int64_t p0 = b; p0 < e; p0 += 32 * kU) {
-        int c[kU];
+        uint8_t f[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) f[u] = (c[u] >= 0) ? __ldcg(P.in_slots + c[u]) : 0;
+        int cn[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            const int64_t p = p0 + 32 * u + lane;
-            c[u] = (p < e) ? __ldg(cols + p) : -1;
+            const int64_t p = p0 + 32 * (kU + u) + lane;
+            cn[u] = (p < e) ? __ldcs(P.csr_cols + p) : -1;
         }
         double vj[kU];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) vj[u] = (c[u] >= 0) ? __ldcg(v + c[u]) : 0.0;
+        for (int u = 0; u < kU; ++u) vj[u] = f[u] ? __ldcg(P.x_hat + c[u]) : 0.0;
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             unsigned nz = __ballot_sync(0xffffffffu, vj[u] != 0.0);
@@ -402,13 +416,16 @@ __device__ __forceinline__ double warp_ordered_row_sum(const int64_t *ptr, const
                 s = __dadd_rn(s, __shfl_sync(0xffffffffu, vj[u], src));
             }
         }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) c[u] = cn[u];
     }
     return s;
 }
 
 // For the lanes whose row has more contributors than its slot record holds
 // (`over`), the row sum by the whole warp, one such row after another; 0.0
-// in the other lanes.  Every lane of the warp must call it.
+// in the other lanes.  Every lane of the warp must call it.  The in-slots
+// flags must be current (ordered residual form).
 __device__ __forceinline__ double overflow_row_sums(const ProblemDev &P, bool over, int i,
                                                    int lane) {
     double mine = 0.0;
@@ -417,7 +434,7 @@ __device__ __forceinline__ double overflow_row_sums(const ProblemDev &P, bool ov
         const int src = __ffs(ov) - 1;
         ov &= ov - 1;
         const int row = __shfl_sync(0xffffffffu, i, src);
-        const double s = warp_ordered_row_sum(P.csr_ptr, P.csr_cols, P.x_hat, row, lane);
+        const double s = warp_ordered_row_sum_flagged(P, row, lane);
         if (lane == src) mine = s;
     }
     return mine;

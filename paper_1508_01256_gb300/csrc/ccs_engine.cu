@@ -383,6 +383,8 @@ int engine_run(ProblemDev *pds, int P, const ccs_params &prm, ccs_result *out, c
         out[p].error = herr ? CCS_ETIMEOUT : CCS_OK;
         out[p].row_driven = hc.row_driven;
         out[p].row_entries = hc.row_entries;
+        out[p].residual_form = hc.ordered ? CCS_RESIDUAL_ORDERED : CCS_RESIDUAL_EXACT;
+        out[p].reserved = 0;
         max_it = std::max(max_it, hc.iteration);
     }
     if (a.stamps) prof_keep_stamps(hst.data(), (int)hst.size(), kSubBase);

@@ -1286,7 +1286,7 @@ static __device__ __noinline__ long long residual_tile(const ProblemDev &P, int 
 
 // A listed overflow row, by one warp; returns the row's change of ||r||_0.
 static __device__ __noinline__ long long residual_overflow_row(const ProblemDev &P, int i, int lane) {
-    const double s = warp_ordered_row_sum(P.csr_ptr, P.csr_cols, P.x_hat, i, lane);
+    const double s = warp_ordered_row_sum_flagged(P, i, lane);
     long long delta = 0;
     if (lane == 0) {
         const double rn = __dsub_rn(__ldg(P.y + i), s);
@@ -1687,6 +1687,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
             res.error = __ldcg(&a.sync->error) ? CCS_ETIMEOUT : CCS_OK;
             res.row_driven = P.ctrl->row_driven;
             res.row_entries = P.ctrl->row_entries;
+            res.residual_form = P.ctrl->ordered ? CCS_RESIDUAL_ORDERED : CCS_RESIDUAL_EXACT;
+            res.reserved = 0;
             a.dev_out[P.out_slot] = res;
         }
     }

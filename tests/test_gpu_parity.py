@@ -403,11 +403,16 @@ def test_residual_modes_match_oracle(ccs, orc, case, flags):
     """The persistent engine keeps r by exact atomic updates while its
     certificate holds, else by ordered row sums; debug bit 1 forces the
     ordered form from the start, bit 2 a switch at iteration 2 (its records
-    rebuilt on the way).  Every form equals the oracle bit for bit."""
+    rebuilt on the way).  Every form equals the oracle bit for bit, and the
+    result reports the form the decode ended in."""
     p = dict(RESIDUAL_CASES)[case]()
     g, ref = _decode_both(ccs, orc, p, engine=ccs.ENGINE_PERSISTENT, debug_flags=flags,
                           max_iter=40)
     assert_same_decode(g, ref)
+    if flags == 2 or (flags == 4 and g.iterations > 2):
+        assert g.residual_form == ccs.RESIDUAL_ORDERED
+    elif flags == 0 and p.model == "gauss-grid" and g.status == ccs.CONVERGED:
+        assert g.residual_form == ccs.RESIDUAL_EXACT
 
 
 def test_residual_mode_switch_in_batch(ccs, orc):
