@@ -622,7 +622,7 @@ template <int DMAX, int THREADS, bool kExactD, bool kWide>
 __device__ __forceinline__ void consume_segment(const EngineArgs &a, const ProblemDev &P,
                                                 const Segment &sg, int per, int nchunks,
                                                 unsigned chunk_seq, ScoreSmem &S, int *wb,
-                                                bool exact, int spos, bool &ok) {
+                                                bool exact, int spos, bool zero_x, bool &ok) {
     constexpr int kTpw = (THREADS == 512) ? 2 : 1;
     const int warps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -654,6 +654,13 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
             const int base = tile * kTile;
             const bool live = lane < P.n - base;
             const int j = base + lane;
+            // first score phase of a lone problem: x_hat <- 0 (Alg. 2's first
+            // line) is stored here, one coalesced line a tile, while the
+            // stream has bandwidth to spare, instead of in a pass of its own;
+            // every later read of x_hat_j follows this store in the same
+            // thread, after a __syncwarp (buffered columns) or after a
+            // __syncthreads (queued columns)
+            if (zero_x && live) P.x_hat[j] = 0.0;
             const int e0 = (j - (int)col0) * d;  // first int of column j in the stage
             int32_t rows[DMAX];
             if (!tail) {
@@ -752,11 +759,14 @@ __device__ __forceinline__ void consume_segment(const EngineArgs &a, const Probl
 // nonzero enter their rows' contributor records, and every column's in-slots
 // flag is set from x_hat (r itself is exact and current, so no row is marked
 // touched).
+// x_zero: x_hat is known to be zero (it is not read: the first score phase of
+// a lone problem has not stored it yet).
 template <int DMAX>
-__device__ __forceinline__ void enter_segment_slots(const ProblemDev &P, int seg_lo, int seg_hi) {
+__device__ __forceinline__ void enter_segment_slots(const ProblemDev &P, int seg_lo, int seg_hi,
+                                                    bool x_zero = false) {
     const long long c1 = min((long long)P.n, (long long)seg_hi * kTile);
     for (long long j = (long long)seg_lo * kTile + threadIdx.x; j < c1; j += blockDim.x) {
-        const bool nz = __ldcg(P.x_hat + j) != 0.0;
+        const bool nz = !x_zero && __ldcg(P.x_hat + j) != 0.0;
         P.in_slots[j] = nz ? 1 : 0;
         if (nz) {
             int32_t rows[DMAX];
@@ -773,7 +783,7 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
                                               int seg_lo, int seg_hi, int g, int it, int rmode,
                                               ScoreSmem &S, unsigned &chunk_seq,
                                               unsigned &fp_seq, bool &ok,
-                                              Prefetch *pf = nullptr) {
+                                              Prefetch *pf = nullptr, bool zero_x = false) {
     const bool exact = rmode == 0;
     const int spos = a.shifted ? it % P.d : -1;  // shifted variant: candidate row
     const Segment sg{0, seg_lo, seg_hi, 0};
@@ -792,7 +802,7 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
         *S.acc = 0;
         *S.xmax = 0;
     }
-    if (rmode == 2) enter_segment_slots<DMAX>(P, seg_lo, seg_hi);
+    if (rmode == 2) enter_segment_slots<DMAX>(P, seg_lo, seg_hi, zero_x);
     __syncthreads();
 
     if (warp == 0) {
@@ -828,14 +838,14 @@ __device__ __forceinline__ void score_segment(const EngineArgs &a, const Problem
         const bool wide = fp16_for(P.m);
         if (P.d == DMAX) {
             if (wide)
-                consume_segment<DMAX, THREADS, true, true>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, spos, ok);
+                consume_segment<DMAX, THREADS, true, true>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, spos, zero_x, ok);
             else
-                consume_segment<DMAX, THREADS, true, false>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, spos, ok);
+                consume_segment<DMAX, THREADS, true, false>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, spos, zero_x, ok);
         } else {
             if (wide)
-                consume_segment<DMAX, THREADS, false, true>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, spos, ok);
+                consume_segment<DMAX, THREADS, false, true>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, spos, zero_x, ok);
             else
-                consume_segment<DMAX, THREADS, false, false>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, spos, ok);
+                consume_segment<DMAX, THREADS, false, false>(a, P, sg, per, nchunks, chunk_seq, S, wb, exact, spos, zero_x, ok);
         }
     }
     chunk_seq += nchunks;
@@ -1451,12 +1461,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
 
     // ---- init: x_hat <- 0, r <- y (Alg. 2, first line) --------------------
     if (!a.probs) {
-        // one problem: grid-stride over its columns and rows
-        // (the in-slots flags are set when the ordered residual begins)
+        // one problem: grid-stride over its rows (x_hat <- 0 is stored by
+        // the first score phase's stream, or below if the decode stops at
+        // once; the in-slots flags are set when the ordered residual begins)
         const ProblemDev &P = a.single;
         const long long gtid = blockIdx.x * (long long)THREADS + threadIdx.x;
         const long long gstride = (long long)gridDim.x * THREADS;
-        for (long long j = gtid; j < P.n; j += gstride) P.x_hat[j] = 0.0;
         for (long long w = gtid; w < (P.n + 3) / 4; w += gstride) P.hits[w] = 0u;
         init_stats_begin(s_sum, s_umax, s_gridb, s_deg);
         InitStats st;
@@ -1511,6 +1521,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
         }
     }
     __syncthreads();
+    if (!a.probs && s_status[0] != kRunning) {
+        // a lone problem that stops before its first score phase (y == 0 or
+        // max_iter == 0): x_hat <- 0 here
+        const long long gtid = blockIdx.x * (long long)THREADS + threadIdx.x;
+        for (long long j = gtid; j < a.single.n; j += (long long)gridDim.x * THREADS)
+            a.single.x_hat[j] = 0.0;
+    }
     issue_ahead(0);
 
     for (int g = 0; g < a.iter_budget; ++g) {
@@ -1550,7 +1567,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_engine(const __grid_constant__ E
                 ++fp_seq;
             } else if (t1 > t0)
                 score_segment<DMAX, THREADS>(a, a.single, t0, t1, g, it, s_rmode[0], S,
-                                             chunk_seq, fp_seq, ok, &pf);
+                                             chunk_seq, fp_seq, ok, &pf, /*zero_x=*/g == 0);
         } else {
             build_partition<THREADS>(a, s_status, s_pref, kPartScore);
             for_my_segments(a, s_status, s_pref, kPartScore,
