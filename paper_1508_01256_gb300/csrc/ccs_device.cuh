@@ -409,7 +409,7 @@ __device__ __forceinline__ double warp_ordered_row_sum_flagged(const ProblemDev 
         for (int u = 0; u < kU; ++u) vj[u] = f[u] ? __ldcg(P.x_hat + c[u]) : 0.0;
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            unsigned nz = __ballot_sync(0xffffffffu, vj[u] != 0.0);
+            unsigned nz = __ballot_sync(0xffffffffu, value_bits(vj[u]) != 0ull);
             while (nz) {
                 const int src = __ffs(nz) - 1;
                 nz &= nz - 1;

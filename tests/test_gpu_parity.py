@@ -257,6 +257,17 @@ def test_edge_slot_overflow_rows(ccs, orc):
     assert_same_decode(g, ref)
 
 
+@pytest.mark.parametrize("flags", [2, 4])
+def test_overflow_rows_under_ordered_residual(ccs, orc, flags):
+    """Rows of up to ~50 nonzero contributors under the ordered residual
+    (bit 1: from the first iteration; bit 2: from iteration 2), so their
+    sums walk the whole CSR row: bit-identical to the oracle."""
+    n, m, d = 4000, 60, 7
+    p = inputs.make_problem(n, m, d, 400, 77)
+    g, ref = _decode_both(ccs, orc, p, max_iter=20, debug_flags=flags)
+    assert_same_decode(g, ref)
+
+
 def _affine_plane(q):
     lines = [sorted(a * q + (s * a + c) % q for a in range(q)) for s in range(q) for c in range(q)]
     lines += [sorted(c * q + b for b in range(q)) for c in range(q)]
