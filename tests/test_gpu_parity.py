@@ -140,6 +140,33 @@ def test_decode_extreme_dense_residual_full(ccs, orc):
     assert g.iterations == 3
 
 
+@pytest.mark.parametrize("rho,seed", [(0.15, 20151510), (0.20, 20151511), (0.30, 20151513)])
+def test_decode_extreme_dense_full_final_state(ccs, orc, rho, seed):
+    """n = 2^24, m = 16777, d = 9 past the transition (the bench's seeds):
+    the decodes run 64 to 100 iterations, through cascades where hundreds of
+    thousands of columns are accepted at once and every row outgrows its
+    record, and stall or reach max_iter.  Too long for the oracle to replay
+    whole here, so the final state is checked against what the oracle fixes
+    at any size: r is the oracle's ordered residual y - A x_hat of the
+    returned x_hat, bit for bit; ||r||_0 is the history's last entry; and a
+    stalled decode's r is one on which the oracle's score of every column
+    accepts none."""
+    p = inputs.extreme_undersampling(rho, d=9, seed=seed)
+    csc, ptr, cols, y = device_problem(ccs, p)
+    g = ccs.decode_parallel_l0(csc, ptr, cols, y)
+    assert g.status in (ccs.STALLED, ccs.MAX_ITER) and g.iterations > 3
+    A, y_ref = oracle_problem(orc, p)
+    assert np.array_equal(y.cpu().numpy().view(np.int64), y_ref.view(np.int64))
+    r_ref = orc.residual(A, p.m, y_ref, g.x_hat.cpu().numpy())
+    assert np.array_equal(g.r.cpu().numpy().view(np.int64), r_ref.view(np.int64))
+    assert g.r0_final == orc.l0(r_ref) == g.r0_hist[-1]
+    if g.status == ccs.STALLED:
+        acc, _, _ = orc.score_all(A, r_ref)
+        assert not acc.any()
+    else:
+        assert g.iterations == 100
+
+
 def test_batch_both_fingerprint_widths(ccs, orc):
     """One batch with problems on both sides of the 16-bit fingerprint limit
     (m <= 32768 keeps 16-bit fingerprints, larger m 8-bit ones), d <= 8 and
