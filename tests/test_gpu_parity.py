@@ -367,6 +367,27 @@ def test_shifted_empty_iterations_on_gpu(ccs, orc, case):
     assert_same_decode(outs[1], orc.parallel_l0(A2, big.m, y2, shifted=True))
 
 
+@pytest.mark.parametrize("case", ["y_zero", "max_iter_zero"])
+def test_decode_stopping_at_once_zeroes_dirty_x_hat(ccs, orc, case):
+    """A lone problem's x_hat <- 0 is stored by its first score phase; a
+    decode that stops before one (y = 0, or max_iter = 0) zeroes x_hat after
+    the init barrier.  Outputs filled with NaN beforehand come back equal to
+    the oracle's, twice on the same buffers."""
+    import torch
+    p = inputs.make_problem(4096, 410, 7, 0 if case == "y_zero" else 41, 5)
+    kw = {"max_iter": 0} if case == "max_iter_zero" else {}
+    csc, ptr, cols, y = device_problem(ccs, p)
+    A, y_ref = oracle_problem(orc, p)
+    ref = orc.parallel_l0(A, p.m, y_ref, **kw)
+    x_hat = torch.full((p.n,), float("nan"), dtype=torch.float64, device="cuda")
+    r = torch.full((p.m,), float("nan"), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        g = ccs.decode_parallel_l0(csc, ptr, cols, y, out=(x_hat, r, None), **kw)
+        assert_same_decode(g, ref, check_hist=False)
+        assert g.iterations == 0
+        x_hat.fill_(float("nan"))
+
+
 def test_workspace_reuse_and_dirty_outputs(ccs, orc):
     """A reused workspace and garbage in the output buffers change nothing."""
     import torch
